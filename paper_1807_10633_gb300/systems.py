@@ -1,0 +1,311 @@
+"""Seeded synthetic inputs: Hamiltonians, wavefunction parameters, initial determinants.
+
+This module is shared by the CUDA path, the oracle and the tests.  It holds no arithmetic
+of the VMC method itself (no local energy, ratio, sampling or optimisation step): it only
+produces the integrals that define the Hamiltonian (Sec. II.A uses h_ij and <ab|ij>), the
+parameters of the Jastrow-Slater wavefunction (Sec. III.A) and starting determinants.
+
+Conventions used everywhere in this project
+-------------------------------------------
+* M spatial orbitals, 2M spin orbitals; spin orbital p = sigma*M + k (alpha block first).
+* h1[p, q]                  one-electron integrals <p|h|q>, real symmetric, shape (M, M).
+* eri[p, q, r, s] = (pq|rs) two-electron integrals in chemists' notation, shape (M,)*4,
+  real orbitals, 8-fold symmetric.  The physicists' <pq|rs> of the paper is (pr|qs).
+* e_core                    constant energy (nuclear repulsion), added to every E_L.
+* J, shape (2M, 2M)         symmetric pair-Jastrow over spin orbitals; J[p, p] is the
+  one-body term d_p.  ln C[n] = sum_{p<q} J_pq n_p n_q + sum_p J_pp n_p.
+* C_alpha (M, n_alpha), C_beta (M, n_beta)  Slater coefficients theta of Sec. III.A.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.special import erf
+
+# STO-3G hydrogen 1s contraction (exponents, contraction coefficients).
+STO3G_H_EXP = np.array([3.42525091, 0.62391373, 0.16885540])
+STO3G_H_COEF = np.array([0.15432897, 0.53532814, 0.44463454])
+
+MASTER_SEED = 1807
+
+
+@dataclass
+class System:
+    """A Hamiltonian in an orthonormal orbital basis plus electron counts."""
+    name: str
+    M: int
+    n_alpha: int
+    n_beta: int
+    h1: np.ndarray            # (M, M) float64
+    eri: np.ndarray           # (M, M, M, M) float64, chemists' (pq|rs)
+    e_core: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_elec(self) -> int:
+        return self.n_alpha + self.n_beta
+
+
+# ---------------------------------------------------------------------------------------
+# Hubbard model (Sec. IV.C uses the 2-D Hubbard model; the 1-D ring is a small test case)
+# ---------------------------------------------------------------------------------------
+def hubbard(Lx: int, Ly: int = 1, t: float = 1.0, U: float = 4.0,
+            n_alpha: int | None = None, n_beta: int | None = None) -> System:
+    """Periodic Hubbard lattice: h_ij = -t for nearest neighbours, (ii|ii) = U."""
+    M = Lx * Ly
+    h1 = np.zeros((M, M))
+
+    def site(x, y):
+        return (y % Ly) * Lx + (x % Lx)
+
+    for y in range(Ly):
+        for x in range(Lx):
+            s = site(x, y)
+            nbrs = []
+            if Lx > 1:
+                nbrs += [site(x + 1, y), site(x - 1, y)]
+            if Ly > 1:
+                nbrs += [site(x, y + 1), site(x, y - 1)]
+            for nb in set(nbrs):
+                if nb != s:
+                    h1[s, nb] = -t
+    eri = np.zeros((M, M, M, M))
+    for s in range(M):
+        eri[s, s, s, s] = U
+    na = M // 2 if n_alpha is None else n_alpha
+    nb = M // 2 if n_beta is None else n_beta
+    name = f"hubbard{Lx}" if Ly == 1 else f"hubbard{Lx}x{Ly}"
+    return System(name, M, na, nb, h1, eri, 0.0, dict(t=t, U=U, Lx=Lx, Ly=Ly))
+
+
+# ---------------------------------------------------------------------------------------
+# Linear hydrogen chain, STO-3G, Loewdin-orthogonalised (local) orbitals
+# ---------------------------------------------------------------------------------------
+def _boys0(x: np.ndarray) -> np.ndarray:
+    """Boys function F0(x) = 1/2 sqrt(pi/x) erf(sqrt(x)); series near 0."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    small = x < 1e-8
+    xs = x[small]
+    out[small] = 1.0 - xs / 3.0 + xs * xs / 10.0
+    xl = x[~small]
+    out[~small] = 0.5 * np.sqrt(np.pi / xl) * erf(np.sqrt(xl))
+    return out
+
+
+def _sgauss_ao_integrals(centers: np.ndarray, charges: np.ndarray, exps: np.ndarray,
+                         coefs: np.ndarray, pair_cut: float = 1e-15):
+    """Overlap S, core Hamiltonian h and ERIs (chemists') over contracted s-Gaussians.
+
+    Closed forms for normalised s primitives (textbook Gaussian product theorem):
+      S   = (pi/p)^{3/2} K_AB
+      T   = ab/p (3 - 2 ab/p R_AB^2) (pi/p)^{3/2} K_AB
+      V_C = -2 pi/p Z_C K_AB F0(p R_PC^2)
+      ERI = 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD F0(p q/(p+q) R_PQ^2)
+    with p = a+b, K_AB = exp(-ab/p R_AB^2), P = (aA+bB)/p.
+    """
+    nb = centers.shape[0]
+    npr = exps.size
+    norm = (2.0 * exps / np.pi) ** 0.75
+    d = coefs * norm                                  # (npr,)
+    # all primitive pairs of all AO pairs
+    A = centers[:, None, None, None, :]
+    B = centers[None, :, None, None, :]
+    a = exps[None, None, :, None]
+    b = exps[None, None, None, :]
+    p = a + b
+    R2 = np.sum((A - B) ** 2, axis=-1)                # (nb, nb, 1, 1)
+    K = np.exp(-a * b / p * R2)
+    P = (a[..., None] * A + b[..., None] * B) / p[..., None]   # (nb, nb, npr, npr, 3)
+    dd = d[None, None, :, None] * d[None, None, None, :]
+    S = np.sum(dd * (np.pi / p) ** 1.5 * K, axis=(2, 3))
+    T = np.sum(dd * a * b / p * (3.0 - 2.0 * a * b / p * R2) * (np.pi / p) ** 1.5 * K,
+               axis=(2, 3))
+    V = np.zeros((nb, nb))
+    for c in range(centers.shape[0]):
+        RPC2 = np.sum((P - centers[c]) ** 2, axis=-1)
+        V -= np.sum(dd * 2.0 * np.pi / p * charges[c] * K * _boys0(p * RPC2), axis=(2, 3))
+    h = T + V
+
+    # ERIs: keep AO pairs (mu<=nu) whose pair prefactor is not negligible
+    coef_pair = dd * K                                # (nb, nb, npr, npr)
+    mu, nu = np.triu_indices(nb)
+    keep = np.max(np.abs(coef_pair[mu, nu]).reshape(mu.size, -1), axis=1) > pair_cut
+    mu, nu = mu[keep], nu[keep]
+    npair = mu.size
+    cp = coef_pair[mu, nu].reshape(npair, npr * npr)
+    pp = np.broadcast_to(p, (nb, nb, npr, npr))[mu, nu].reshape(npair, npr * npr)
+    PP = P[mu, nu].reshape(npair, npr * npr, 3)
+    eri_pairs = np.zeros((npair, npair))
+    chunk = max(1, 2_000_000 // (npair * npr ** 4) + 1)
+    for i0 in range(0, npair, chunk):
+        i1 = min(npair, i0 + chunk)
+        pa = pp[i0:i1, None, :, None]                  # (c, 1, 9, 1)
+        qa = pp[None, :, None, :]                      # (1, np, 1, 9)
+        R2pq = np.sum((PP[i0:i1, None, :, None, :] - PP[None, :, None, :, :]) ** 2, axis=-1)
+        pref = 2.0 * np.pi ** 2.5 / (pa * qa * np.sqrt(pa + qa))
+        val = pref * _boys0(pa * qa / (pa + qa) * R2pq)
+        val *= cp[i0:i1, None, :, None] * cp[None, :, None, :]
+        eri_pairs[i0:i1] = val.sum(axis=(2, 3))
+    eri = np.zeros((nb, nb, nb, nb))
+    eri[mu[:, None], nu[:, None], mu[None, :], nu[None, :]] = eri_pairs
+    eri[nu[:, None], mu[:, None], mu[None, :], nu[None, :]] = eri_pairs
+    eri[mu[:, None], nu[:, None], nu[None, :], mu[None, :]] = eri_pairs
+    eri[nu[:, None], mu[:, None], nu[None, :], mu[None, :]] = eri_pairs
+    return S, h, eri
+
+
+def _transform_eri(eri: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """(pq|rs) <- sum X[mu,p] X[nu,q] X[la,r] X[si,s] (mu nu|la si), four quarter steps."""
+    M = X.shape[0]
+    T = eri
+    for _ in range(4):
+        T = (X.T @ T.reshape(M, -1)).reshape(M, M, M, M)
+        T = np.ascontiguousarray(np.moveaxis(T, 0, 3))
+    return T
+
+
+def hchain(n_atoms: int, spacing: float = 1.8) -> System:
+    """Linear H_n chain in STO-3G, integrals in Loewdin-orthogonalised AOs (local orbitals)."""
+    centers = np.zeros((n_atoms, 3))
+    centers[:, 0] = spacing * np.arange(n_atoms)
+    charges = np.ones(n_atoms)
+    S, h, eri_ao = _sgauss_ao_integrals(centers, charges, STO3G_H_EXP, STO3G_H_COEF)
+    s, U = np.linalg.eigh(S)
+    X = (U * s ** -0.5) @ U.T                          # S^{-1/2}, symmetric
+    h1 = X.T @ h @ X
+    h1 = 0.5 * (h1 + h1.T)
+    eri = _transform_eri(eri_ao, X)
+    del eri_ao
+    e_core = 0.0
+    for A in range(n_atoms):
+        for B in range(A + 1, n_atoms):
+            e_core += 1.0 / (spacing * (B - A))
+    na = (n_atoms + 1) // 2
+    nb = n_atoms // 2
+    return System(f"H{n_atoms}", n_atoms, na, nb, h1, eri, e_core,
+                  dict(spacing=spacing, basis="sto-3g", orbitals="lowdin"))
+
+
+# ---------------------------------------------------------------------------------------
+# Wavefunction parameters (Sec. III.A; pair Jastrow = two-site correlators)
+# ---------------------------------------------------------------------------------------
+@dataclass
+class Params:
+    J: np.ndarray            # (2M, 2M) symmetric; diagonal = one-body terms
+    C_alpha: np.ndarray      # (M, n_alpha)
+    C_beta: np.ndarray       # (M, n_beta)
+
+    def flat(self) -> np.ndarray:
+        return np.concatenate([self.J.ravel(), self.C_alpha.ravel(), self.C_beta.ravel()])
+
+
+def random_jastrow(M: int, rng: np.random.Generator, scale: float = 0.01) -> np.ndarray:
+    A = rng.normal(0.0, scale, size=(2 * M, 2 * M))
+    J = np.triu(A) + np.triu(A, 1).T
+    return J
+
+
+def planewave_ring(L: int, n: int) -> np.ndarray:
+    """Real plane waves on a ring: 1, cos(2 pi k x/L), sin(2 pi k x/L), k = 1, 2, ..."""
+    x = np.arange(L)
+    cols = [np.ones(L)]
+    k = 1
+    while len(cols) < n:
+        cols.append(np.cos(2 * np.pi * k * x / L))
+        if len(cols) < n:
+            cols.append(np.sin(2 * np.pi * k * x / L))
+        k += 1
+    C = np.stack(cols, axis=1)
+    return C / np.linalg.norm(C, axis=0)
+
+
+def core_orbitals(h1: np.ndarray, n: int) -> np.ndarray:
+    """Lowest n eigenvectors of h1 (core-Hamiltonian guess), sign-fixed."""
+    _, V = np.linalg.eigh(h1)
+    V = V[:, :n].copy()
+    for c in range(n):
+        if V[np.argmax(np.abs(V[:, c])), c] < 0:
+            V[:, c] *= -1
+    return V
+
+
+def make_params(sys: System, seed: int = MASTER_SEED, j_scale: float = 0.01,
+                c_noise: float = 0.01, zero_jastrow: bool = False,
+                exact_planewave: bool = False) -> Params:
+    """Seeded Jastrow-Slater parameters.
+
+    Slater part: Hubbard rings use real plane waves, everything else the core-Hamiltonian
+    orbitals; both get an independent N(0, c_noise) perturbation per spin (unrestricted).
+    Jastrow: J ~ N(0, j_scale), symmetric, over spin-orbital pairs.
+    """
+    rng = np.random.default_rng(seed)
+    M = sys.M
+    J = np.zeros((2 * M, 2 * M)) if zero_jastrow else random_jastrow(M, rng, j_scale)
+    if sys.name.startswith("hubbard") and sys.meta.get("Ly", 1) == 1:
+        Ca = planewave_ring(M, sys.n_alpha)
+        Cb = planewave_ring(M, sys.n_beta)
+    else:
+        Ca = core_orbitals(sys.h1, sys.n_alpha)
+        Cb = core_orbitals(sys.h1, sys.n_beta)
+    if not exact_planewave:
+        Ca = Ca + rng.normal(0.0, c_noise, size=Ca.shape)
+        Cb = Cb + rng.normal(0.0, c_noise, size=Cb.shape)
+    return Params(J, np.ascontiguousarray(Ca), np.ascontiguousarray(Cb))
+
+
+# ---------------------------------------------------------------------------------------
+# Starting determinants (the paper is silent; seeded random, well-conditioned)
+# ---------------------------------------------------------------------------------------
+def _well_conditioned(C: np.ndarray, occ: np.ndarray, tol: float) -> bool:
+    sv = np.linalg.svd(C[occ], compute_uv=False)
+    return sv[-1] > tol * sv[0]
+
+
+def init_occupations(sys: System, prm: Params, W: int, seed: int = MASTER_SEED + 1,
+                     cond_tol: float = 1e-6) -> np.ndarray:
+    """Per-walker occupied orbital lists, shape (W, n_alpha + n_beta), uint16, each spin
+    block sorted ascending (alpha orbitals then beta orbitals, spatial indices 0..M-1).
+    A draw is redone while the occupied rows of C are badly conditioned."""
+    rng = np.random.default_rng(seed)
+    M, na, nb = sys.M, sys.n_alpha, sys.n_beta
+    out = np.empty((W, na + nb), dtype=np.uint16)
+    for w in range(W):
+        for _ in range(1000):
+            oa = np.sort(rng.choice(M, na, replace=False))
+            ob = np.sort(rng.choice(M, nb, replace=False))
+            if _well_conditioned(prm.C_alpha, oa, cond_tol) and \
+               _well_conditioned(prm.C_beta, ob, cond_tol):
+                break
+        else:
+            raise RuntimeError("could not draw a well-conditioned determinant")
+        out[w, :na] = oa
+        out[w, na:] = ob
+    return out
+
+
+def occ_to_bits(occ: np.ndarray, M: int, n_alpha: int) -> np.ndarray:
+    """(W, n_e) occupied lists -> (W, 2, ceil(M/32)) uint32 bitstrings per spin."""
+    W = occ.shape[0]
+    nw = (M + 31) // 32
+    bits = np.zeros((W, 2, nw), dtype=np.uint32)
+    for w in range(W):
+        for c, k in enumerate(occ[w]):
+            s = 0 if c < n_alpha else 1
+            bits[w, s, int(k) // 32] |= np.uint32(1 << (int(k) % 32))
+    return bits
+
+
+def named_system(name: str) -> System:
+    """Workloads by name: 'hubbard10', 'hubbard4x4', 'H20', ..."""
+    if name.startswith("hubbard"):
+        dims = name[len("hubbard"):]
+        if "x" in dims:
+            lx, ly = (int(v) for v in dims.split("x"))
+            return hubbard(lx, ly, t=1.0, U=4.0)
+        return hubbard(int(dims), 1, t=1.0, U=4.0)
+    if name.startswith("H"):
+        return hchain(int(name[1:]))
+    raise ValueError(name)
