@@ -336,3 +336,35 @@ def test_amsgrad_hand_recurrence():
     p = np.array([2.0]); m = np.zeros(1); v = np.zeros(1)
     oracle.amsgrad(p, np.array([0.0]), m, v, alpha, b1, b2)
     assert p[0] == 2.0
+
+
+def test_singles_screen_uses_two_electron_bound():
+    """With the off-diagonal one-electron integrals removed, singles survive the screen only
+    through the sum over j in S_ia (Sec. II.A); the filtered brute force must agree."""
+    sys = _h6()
+    sys.h1 = np.diag(np.diag(sys.h1)).copy()
+    prm = S.make_params(sys, seed=3, j_scale=0.05, c_noise=0.1)
+    dets, H = brute.hamiltonian(sys)
+    n = brute.occupations(dets, sys.M)
+    psi = brute.psi_all(n, sys.M, prm)
+    Sia = brute.singles_bound(sys)
+    vals = np.unique(np.round(Sia[~np.eye(sys.M, dtype=bool)], 12))
+    mid = len(vals) // 2
+    eps = float(0.5 * (vals[mid] + vals[mid + 1]))   # away from any S_ia (no near-ties)
+    M = sys.M
+    Hc = H.tocoo()
+    el_ref = np.zeros(len(dets))
+    n_single_kept = 0
+    for r, c, v in zip(Hc.row, Hc.col, Hc.data):
+        if r == c:
+            el_ref[r] += v
+            continue
+        diff = int(dets[r] ^ dets[c])
+        bits = [k for k in range(2 * M) if (diff >> k) & 1]
+        keep = (Sia[bits[0] % M, bits[1] % M] > eps) if len(bits) == 2 else abs(v) > eps
+        if keep:
+            n_single_kept += len(bits) == 2
+            el_ref[r] += v * psi[c] / psi[r]
+    assert n_single_kept > 0
+    el, _, _ = Oracle(sys, prm).local_energy_batch(n, eps)
+    np.testing.assert_allclose(el, el_ref, rtol=1e-10, atol=1e-10)
