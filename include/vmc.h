@@ -1,0 +1,203 @@
+/*
+ * vmc.h -- C ABI of the GB300 (sm_103a) screened orbital-space VMC hot path.
+ *
+ * Method: Sabzevari & Sharma, "Improved speed and scaling in orbital space variational Monte
+ * Carlo" (arXiv:1807.10633).  The three tasks of Sec. II -- local energy of a determinant,
+ * sampling determinants from rho = |psi|^2, optimising the parameters -- map onto the calls
+ * below.  Every compute step runs in the library's CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ *   - M spatial orbitals, 2M spin orbitals, spin orbital p = sigma*M + k (alpha block first).
+ *   - Integrals: h1[p*M+q] = <p|h|q>; eri[((p*M+q)*M+r)*M+s] = (pq|rs) in chemists' notation
+ *     (real orbitals, 8-fold symmetric).  The paper's physicists' <ab|ij> equals (ai|bj).
+ *   - Wavefunction (Sec. III.A with a pair Jastrow in place of the general correlators):
+ *       psi(n) = exp(sum_{p<q} J_pq n_p n_q + sum_p J_pp n_p) det C^a[n^a] det C^b[n^b].
+ *     J is (2M)x(2M) row-major and is read from its upper triangle (p <= q) only.
+ *     C^sigma is M x n_sigma row-major.
+ *   - All pointers named d_* or stored in vmc_walkers are DEVICE pointers owned by the caller;
+ *     the library never frees them.  Pointers named h_* are host pointers, read during the
+ *     call only.  Work is queued on the context's stream; calls return once it is queued.
+ *   - Every call returns a vmc_status.  Errors found on the device (fixed-point rate overflow,
+ *     a walker with no allowed move, a singular C_occ) are latched in a device status word;
+ *     vmc_sync() waits for the stream and returns the latched error (then clears it).
+ *   - On an error the call leaves its outputs unspecified and vmc_last_error() describes it.
+ */
+#ifndef VMC_H
+#define VMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VMC_OK = 0,
+    VMC_ERR_ARG = 1,       /* invalid argument, size or call order */
+    VMC_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    VMC_ERR_OOM = 3,       /* device or host allocation failed */
+    VMC_ERR_SINGULAR = 4,  /* a C_occ block is singular (|pivot| == 0) */
+    VMC_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    VMC_ERR_OVERFLOW = 6,  /* a CTMC rate reached the fixed-point limit 2^43 */
+    VMC_ERR_NOMOVE = 7     /* a walker had no move with a non-zero fixed-point rate */
+} vmc_status;
+
+typedef enum {
+    VMC_FP64 = 0,          /* G, A^-1, Jastrow sums and ratios in FP64 */
+    VMC_MIXED = 1          /* G, A^-1, Jastrow sums and ratios in FP32; sums, LU, Fock sums FP64 */
+} vmc_precision;
+
+typedef struct vmc_ctx vmc_ctx;       /* device, stream, workspace, status word */
+typedef struct vmc_lists vmc_lists;   /* device-resident screened integral lists */
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL = legacy
+   default stream).  The context allocates a small status word and grows a workspace on demand. */
+vmc_status vmc_create(vmc_ctx **ctx, int device, void *cuda_stream);
+vmc_status vmc_destroy(vmc_ctx *ctx);
+/* Replace the stream used by later calls (cudaStream_t). */
+vmc_status vmc_set_stream(vmc_ctx *ctx, void *cuda_stream);
+/* Text of the last error seen on this context ("" if none); valid until the next call. */
+const char *vmc_last_error(const vmc_ctx *ctx);
+/* Wait for the context's stream; return and clear the latched device status. */
+vmc_status vmc_sync(vmc_ctx *ctx);
+
+/*
+ * Screened integral lists in "heat-bath" form (Sec. II.A).
+ *   same-spin pairs p<q : entries {a<b, v = (ap|bq) - (aq|bp)}, |v| > eps, a,b not in {p,q}
+ *   opposite-spin (p_alpha, q_beta) : entries {a, b, v = (ap|bq)}, |v| > eps, a != p, b != q
+ *   singles i : entries {a != i, S_ia} with S_ia = |h_ia| + sum_j |<ij|aj> - <ij|ja>| > eps
+ *               (j over all spin orbitals), the bound of Sec. II.A
+ * Each list is sorted by magnitude descending (ties: a, then b ascending), so a walk can stop
+ * at the first entry at or below a threshold.  The library also stores, per singles entry,
+ * the Coulomb/exchange columns used to keep each walker's single-excitation elements
+ * h_ai + sum_{j occ} <aj||ij> up to date, and the diagonal Coulomb/exchange tables.
+ *   h_h1 : [M*M] host, h_eri : [M^4] host (dense), e_core : constant added to every E_L.
+ *   eps  : build threshold (>= 0); later calls may walk with any eps_run >= eps.
+ *   M    : 1 <= M <= 256.
+ * The lists are built on the host (once per eps, O(M^4 log M)) and copied to the device.
+ * Free with vmc_lists_destroy.
+ */
+vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double *h_h1, const double *h_eri,
+                                    double e_core, double eps, vmc_lists **out);
+vmc_status vmc_lists_destroy(vmc_lists *lists);
+
+/* Sizes of a list object: number of singles entries (the length of each walker's per-spin
+   Fock-sum vector), same-spin and opposite-spin double entries. */
+vmc_status vmc_lists_info(const vmc_lists *lists, int64_t *n_singles, int64_t *n_same,
+                          int64_t *n_opp);
+
+/*
+ * Walker state (Sec. III.B): one determinant per walker and the tables that make every ratio
+ * O(1).  All arrays are caller-owned device buffers of W walkers, walker-major:
+ *   occ_bits  uint32 [W][2][ceil(M/32)]  occupation bit strings per spin (bit k of spatial k)
+ *   occ_list  uint16 [W][na+nb]     column c -> occupied spatial orbital (alpha cols, beta cols)
+ *   virt_list uint16 [W][(M-na)+(M-nb)]  virtual slot -> unoccupied spatial orbital
+ *   G         real   [W][(M-na)*na + (M-nb)*nb]  virtual rows of G^s = C^s (C^s_occ)^-1,
+ *             row = virtual slot, column = occupied column (Eq. R: G_ac = det ratio of i->a)
+ *   AinvT     real   [W][na*na + nb*nb]  (C^s_occ)^-1 transposed: AinvT[c][x]
+ *   S         real   [W][2M]   Jastrow sums S_p = sum_{k occ, k != p} J_pk
+ *   F         double [W][2][n_singles]  h_ai + sum_{j occ} <aj||ij> for every singles entry
+ *                     (i -> a) and spin (the elements of Sec. II.A, kept up to date per move)
+ *   e_diag    double [W]       <n|H|n> including e_core
+ *   rng_counter uint64 [W]     Philox counter of each walker (advanced by vmc_ctmc_step)
+ * real = double for VMC_FP64, float for VMC_MIXED.  The orbital order inside occ_list and
+ * virt_list is an implementation detail (moves replace entries in place).
+ */
+typedef struct {
+    int W, M, n_alpha, n_beta;
+    int precision;            /* vmc_precision of G, AinvT, S */
+    uint32_t *occ_bits;
+    uint16_t *occ_list;
+    uint16_t *virt_list;
+    void *G;
+    void *AinvT;
+    void *S;
+    double *F;
+    double *e_diag;
+    uint64_t *rng_counter;
+} vmc_walkers;
+
+/* Wavefunction parameters, device pointers: J [(2M)*(2M)], C_alpha [M*na], C_beta [M*nb]. */
+typedef struct {
+    const double *J;
+    const double *C_alpha;
+    const double *C_beta;
+} vmc_params;
+
+/* Element counts of every walker array for W walkers (for allocation by the caller):
+   out[0..9] = occ_bits, occ_list, virt_list, G, AinvT, S, F, e_diag, rng_counter (elements). */
+vmc_status vmc_walkers_sizes(int W, int M, int n_alpha, int n_beta, const vmc_lists *lists,
+                             int64_t out[9]);
+
+/*
+ * (Re)build every walker table from occ_list (each spin block holds the walker's occupied
+ * orbitals in any order) and the parameters: occ_bits, virt_list, C_occ^-1 by FP64 LU with
+ * partial pivoting (the one O(N^3) step of Sec. III.B), G = C C_occ^-1, S, F, e_diag.  Also
+ * refreshes the Jastrow constants stored with the lists for these parameters.  rng_counter is
+ * left as is.  This is the periodic recompute (e.g. every 64 moves, and after every parameter
+ * update).  Singular blocks latch VMC_ERR_SINGULAR.
+ */
+vmc_status vmc_walkers_init(vmc_ctx *ctx, vmc_lists *lists, const vmc_params *params,
+                            vmc_walkers *walkers);
+
+/*
+ * Screened local energy, Eq. (eloc:hci), for every walker:
+ *   E_L[n, eps_run] = e_diag + sum_{i->a kept} H ratio + sum_{ij->ab kept} H ratio
+ * walking each occupied pair's sorted list up to the first |v| <= eps_run (eps_run >= the
+ * build eps).  Ratios use G (Eq. R and its 2x2 minor) and the Jastrow sums.  The same ratios
+ * are the CTMC rates r = |psi(m)/psi(n)| of Eq. (rate); their exact fixed-point sums are kept
+ * in the context's rate store for vmc_ctmc_step, and the residence time t_n = 1/sum r is
+ * returned.  d_e_loc, d_t_res: double [W] device outputs.
+ */
+vmc_status vmc_local_energy(vmc_ctx *ctx, const vmc_lists *lists, const vmc_params *params,
+                            vmc_walkers *walkers, double eps_run, double *d_e_loc,
+                            double *d_t_res);
+
+/*
+ * Continuous-time Monte Carlo move (Sec. II.B): for every walker pick the next determinant with
+ * probability proportional to its rate, without rejection, from the rates stored by the last
+ * vmc_local_energy on the same walkers (which must come first: VMC_ERR_ARG otherwise), then
+ * update the walker in O(N^2): Sherman-Morrison (rank-1, or rank-2 Woodbury for same-spin
+ * doubles) on G and AinvT, Jastrow sums, Fock sums, e_diag, bits and lists.
+ * Choice rule: q_k = floor(r_k 2^64) (exact 128-bit), U = word 0 of
+ * Philox4x64-10(key = (seed, walker index), counter = (rng_counter[w], 0, 0, 0)),
+ * T = floor(U Q / 2^64) with Q = sum q_k; the first move in canonical order whose prefix sum
+ * exceeds T is taken.  Canonical order: singles by (occupied spin orbital i ascending, list
+ * position), then doubles by ((i,j) ascending lexicographically, list position).
+ * d_move_code: uint64 [W] device output, kind | i<<2 | j<<12 | a<<22 | b<<32 (spin orbitals,
+ * kind 1 = single with j = b = 1023, kind 2 = double).  rng_counter advances by one.
+ */
+vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *lists, const vmc_params *params,
+                         vmc_walkers *walkers, uint64_t seed, uint64_t *d_move_code);
+
+/*
+ * Vector-Jacobian product of ln psi (Sec. III.B gradient ratios) for weights w [W] (device):
+ *   d_dJ[p][q]  += sum_w w_w n_p n_q   (p < q),   d_dJ[p][p] += sum_w w_w n_p   (upper triangle)
+ *   d_dC_s[k][x] += sum_w w_w (C^s_occ)^-1[x][col(k)]   for occupied k of spin s
+ * With w = t_n (E_L - E_ref) and w = t_n this gives the pieces of the energy gradient
+ * g = 2 <(E_L - E) d ln psi/dp>, Eq. (grad).  Sums are FP64.
+ */
+vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *walkers, const double *d_w,
+                           double *d_dJ, double *d_dC_alpha, double *d_dC_beta);
+
+/*
+ * AMSGrad, Eqs. (m1)-(m2) as printed (beta1 weights the new gradient):
+ *   m <- (1-beta1) m + beta1 g;  n <- max(n, (1-beta2) n + beta2 g^2);  p <- p - alpha m/sqrt(n)
+ * with no update where n == 0.  All arrays FP64 device, length n_params.
+ */
+vmc_status vmc_amsgrad_update(vmc_ctx *ctx, double *d_p, const double *d_g, double *d_m,
+                              double *d_n, size_t n_params, double alpha, double beta1,
+                              double beta2);
+
+/* Sum over walkers: out[0] += sum t, out[1] += sum t E_L (FP64, device out[2]). */
+vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const double *d_e_loc,
+                             double *d_out);
+
+/* Number of kernel launches this context has issued (for accounting in benchmarks). */
+uint64_t vmc_launch_count(const vmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMC_H */

@@ -295,10 +295,19 @@ static double spin_ratio(const det_tables *t, int sg, int k, const int *from, co
 }
 
 /* ---------------------------------------------------------------- screening quantities */
-/* S_ia = |<i|h|a>| + sum_{j in all spin orbitals} |<ij|aj> - <ij|ja>|   (Sec. II.A) */
+/* S_ia = |<i|h|a>| + sum_{j in all spin orbitals} |<ij|aj> - <ij|ja>|   (Sec. II.A).
+   The sum visits the spin orbitals of i's spin first, then the other spin (each ascending), so
+   that an alpha and a beta single with the same spatial orbitals get bit-identical bounds. */
 static double singles_bound(const orc_system *s, int i, int a) {
     double acc = fabs(h1so(s, i, a));
-    for (int j = 0; j < 2 * s->M; ++j) acc += fabs(phys(s, i, j, a, j) - phys(s, i, j, j, a));
+    const int M = s->M, si = spin_of(s, i);
+    for (int t = 0; t < 2; ++t) {
+        const int sj = t == 0 ? si : 1 - si;
+        for (int k = 0; k < M; ++k) {
+            const int j = sj * M + k;
+            acc += fabs(phys(s, i, j, a, j) - phys(s, i, j, j, a));
+        }
+    }
     return acc;
 }
 
