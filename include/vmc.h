@@ -142,6 +142,22 @@ vmc_status vmc_walkers_init(vmc_ctx *ctx, vmc_lists *lists, const vmc_params *pa
                             vmc_walkers *walkers);
 
 /*
+ * After a parameter update: refresh the parameter-dependent tables only (Jastrow constants of
+ * the lists, C_occ^-1 by FP64 LU, G, S).  F and e_diag depend on the occupations alone and are
+ * kept.  Same errors as vmc_walkers_init.
+ */
+vmc_status vmc_walkers_refresh(vmc_ctx *ctx, vmc_lists *lists, const vmc_params *params,
+                               vmc_walkers *walkers);
+
+/*
+ * ln|psi(n)| per walker (Sec. III.A): the Jastrow sum plus ln|det C^s_occ| of both spins, from
+ * an FP64 LU of each C_occ block (no walker table is used or changed).  d_out: double [W].
+ * A singular block gives -inf and latches VMC_ERR_SINGULAR.
+ */
+vmc_status vmc_log_psi(vmc_ctx *ctx, const vmc_walkers *walkers, const vmc_params *params,
+                       double *d_out);
+
+/*
  * Screened local energy, Eq. (eloc:hci), for every walker:
  *   E_L[n, eps_run] = e_diag + sum_{i->a kept} H ratio + sum_{ij->ab kept} H ratio
  * walking each occupied pair's sorted list up to the first |v| <= eps_run (eps_run >= the

@@ -1,0 +1,358 @@
+// Walker tables (Sec. III.B): the one O(N^3) inverse per determinant and the O(1)-ratio tables
+// built from it -- G = C C_occ^-1 (Eq. R), the Jastrow sums, the single-excitation Fock sums
+// and the diagonal energy.  Also ln|psi| per walker (forward of the ln psi autograd function).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+// Gauss-Jordan elimination with partial pivoting (an LU factorisation whose inverse is
+// accumulated in place) of the n x n FP64 matrix B held in shared memory with row stride ld.
+// X (same layout) receives B^-1.  Returns (in *sing) whether a zero pivot was met.
+__device__ void gj_invert(double *B, double *X, int n, int ld, double *colk, int *s_piv,
+                          int *sing) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < n * ld; t += nt) X[t] = 0.0;
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) X[r * ld + r] = 1.0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int idx = k;
+            for (int r = k + lane; r < n; r += 32) {
+                const double v = fabs(B[r * ld + k]);
+                if (v > best) { best = v; idx = r; }
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, m);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+                if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+            }
+            if (lane == 0) *s_piv = idx;
+        }
+        __syncthreads();
+        const int p = *s_piv;
+        if (p != k) {
+            for (int c = tid; c < 2 * n; c += nt) {
+                double *A = c < n ? B : X;
+                const int cc = c < n ? c : c - n;
+                const double t = A[k * ld + cc];
+                A[k * ld + cc] = A[p * ld + cc];
+                A[p * ld + cc] = t;
+            }
+        }
+        __syncthreads();
+        double d = B[k * ld + k];
+        if (d == 0.0) {
+            if (tid == 0) *sing = 1;
+            d = 1.0;
+        }
+        __syncthreads();
+        for (int c = tid; c < 2 * n; c += nt) {
+            if (c < n) B[k * ld + c] = B[k * ld + c] / d;
+            else X[k * ld + (c - n)] = X[k * ld + (c - n)] / d;
+        }
+        for (int r = tid; r < n; r += nt) colk[r] = B[r * ld + k];
+        __syncthreads();
+        for (int t = tid; t < n * 2 * n; t += nt) {
+            const int r = t / (2 * n), c = t % (2 * n);
+            if (r == k) continue;
+            const double f = colk[r];
+            if (c < n) B[r * ld + c] -= f * B[k * ld + c];
+            else X[r * ld + (c - n)] -= f * X[k * ld + (c - n)];
+        }
+        __syncthreads();
+    }
+}
+
+// LU with partial pivoting in shared memory; returns log|det| and sign (0 if singular).
+__device__ void lu_logdet(double *B, int n, int ld, int *s_piv, double *s_acc, double *logabs,
+                          int *sign) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double s_log;
+    __shared__ int s_sgn;
+    if (tid == 0) { s_log = 0.0; s_sgn = 1; }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int idx = k;
+            for (int r = k + lane; r < n; r += 32) {
+                const double v = fabs(B[r * ld + k]);
+                if (v > best) { best = v; idx = r; }
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, m);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+                if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+            }
+            if (lane == 0) *s_piv = idx;
+        }
+        __syncthreads();
+        const int p = *s_piv;
+        if (p != k) {
+            for (int c = tid; c < n; c += nt) {
+                const double t = B[k * ld + c];
+                B[k * ld + c] = B[p * ld + c];
+                B[p * ld + c] = t;
+            }
+        }
+        __syncthreads();
+        const double d = B[k * ld + k];
+        if (tid == 0) {
+            if (p != k) s_sgn = -s_sgn;
+            if (d == 0.0) s_sgn = 0;
+            else {
+                s_log += log(fabs(d));
+                if (d < 0) s_sgn = -s_sgn;
+            }
+        }
+        for (int t = tid; t < (n - k - 1) * (n - k); t += nt) {
+            const int r = k + 1 + t / (n - k), c = k + t % (n - k);
+            if (c == k) continue;
+            const double f = B[r * ld + k] / (d == 0.0 ? 1.0 : d);
+            B[r * ld + c] -= f * B[k * ld + c];
+        }
+        __syncthreads();
+    }
+    (void)s_acc;
+    *logabs = s_log;
+    *sign = s_sgn;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(VMC_THREADS)
+k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
+              uint16_t *occ_list, uint16_t *virt_list, uint32_t *occ_bits, real *G, real *AinvT,
+              unsigned *status) {
+    const int w = blockIdx.x, sg = blockIdx.y;
+    const int n = sg ? nb : na, nv = M - n;
+    const int ne = na + nb, nw = (M + 31) / 32;
+    const double *C = sg ? Cb : Ca;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double *B = sm;
+    double *X = B + (size_t)n * ld;
+    double *colk = X + (size_t)n * ld;
+    __shared__ uint16_t s_occ[VMC_MAX_M], s_virt[VMC_MAX_M];
+    __shared__ uint8_t mark[VMC_MAX_M];
+    __shared__ int s_piv, s_sing;
+    const uint16_t *occ = occ_list + (size_t)w * ne + (sg ? na : 0);
+    uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
+    for (int k = tid; k < M; k += nt) mark[k] = 0;
+    if (tid == 0) s_sing = 0;
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+        s_occ[c] = occ[c];
+        mark[occ[c]] = 1;
+    }
+    __syncthreads();
+    if (tid == 0) {   // virtual slots: unoccupied orbitals ascending
+        int v = 0;
+        for (int k = 0; k < M; ++k)
+            if (!mark[k]) s_virt[v++] = (uint16_t)k;
+    }
+    for (int q = tid; q < nw; q += nt) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int k = q * 32 + b;
+            if (k < M && mark[k]) word |= 1u << b;
+        }
+        occ_bits[((size_t)w * 2 + sg) * nw + q] = word;
+    }
+    // B = C_occ^T: B[x][c] = C[occ[c]][x]
+    for (int t = tid; t < n * n; t += nt) {
+        const int x = t / n, c = t % n;
+        B[x * ld + c] = C[(size_t)s_occ[c] * n + x];
+    }
+    __syncthreads();
+    for (int s = tid; s < nv; s += nt) vl[s] = s_virt[s];
+    if (n > 0) gj_invert(B, X, n, ld, colk, &s_piv, &s_sing);   // X = (C_occ^T)^-1 = AinvT
+    __syncthreads();
+    if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
+    const size_t gofs = (size_t)w * ((size_t)(M - na) * na + (size_t)(M - nb) * nb) +
+                        (sg ? (size_t)(M - na) * na : 0);
+    const size_t aofs = (size_t)w * ((size_t)na * na + (size_t)nb * nb) + (sg ? (size_t)na * na : 0);
+    for (int t = tid; t < n * n; t += nt) {
+        const int c = t / n, x = t % n;
+        AinvT[aofs + t] = (real)X[c * ld + x];
+    }
+    // G[s][c] = sum_x C[virt[s]][x] Ainv[x][c] = sum_x C[virt[s]][x] AinvT[c][x]
+    for (int t = tid; t < nv * n; t += nt) {
+        const int s = t / n, c = t % n;
+        const double *crow = C + (size_t)s_virt[s] * n;
+        double acc = 0.0;
+        for (int x = 0; x < n; ++x) acc += crow[x] * X[c * ld + x];
+        G[gofs + t] = (real)acc;
+    }
+}
+
+// Jastrow sums S_p, and (full init only) Fock sums and the diagonal energy.
+template <typename real>
+__global__ void __launch_bounds__(VMC_THREADS)
+k_init_sums(ListsView L, int na, int nb, const double *__restrict__ J, const uint16_t *occ_list,
+            real *S, double *F, double *e_diag, int full) {
+    const int w = blockIdx.x, M = L.M, N2 = 2 * M, ne = na + nb;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_so[2 * VMC_MAX_M];   // occupied spin orbitals
+    __shared__ double red[VMC_WARPS];
+    const uint16_t *occ = occ_list + (size_t)w * ne;
+    for (int c = tid; c < ne; c += nt) s_so[c] = (c < na ? 0 : M) + occ[c];
+    __syncthreads();
+    for (int p = tid; p < N2; p += nt) {
+        double acc = 0.0;
+        for (int c = 0; c < ne; ++c) {
+            const int k = s_so[c];
+            if (k != p) acc += jget(J, N2, p, k);
+        }
+        S[(size_t)w * N2 + p] = (real)acc;
+    }
+    if (!full) return;
+    // F[s][e] = h_ai + sum_{j occ, spin s} Tjk[j][e] + sum_{j occ, other spin} Tj[j][e]
+    for (int64_t e = tid; e < L.ns; e += nt) {
+        const int i = (int)L.s_owner[e], a = L.s_a[e];
+        const double h = L.h1[(size_t)a * M + i];
+        for (int s = 0; s < 2; ++s) {
+            double acc = h;
+            for (int c = 0; c < ne; ++c) {
+                const int js = c < na ? 0 : 1;
+                const int j = occ[c];
+                acc += (js == s ? L.Tjk : L.Tj)[(size_t)j * L.ns + e];
+            }
+            F[((size_t)w * 2 + s) * L.ns + e] = acc;
+        }
+    }
+    // e_diag = e_core + sum_p h_pp + 1/2 sum_{p != q} [(pp|qq) - delta_s (pq|qp)]
+    double part = 0.0;
+    for (int t = tid; t < ne * ne; t += nt) {
+        const int x = t / ne, y = t % ne;
+        const int p = s_so[x], q = s_so[y];
+        const int kp = p % M, kq = q % M;
+        if (x == y) {
+            part += L.hd[kp];
+        } else {
+            double d = L.Jd[(size_t)kp * M + kq];
+            if ((p >= M) == (q >= M)) d -= L.Kd[(size_t)kp * M + kq];
+            part += 0.5 * d;
+        }
+    }
+    part = warp_sum_f64(part);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+        double s = L.e_core;
+        for (int k = 0; k < (nt >> 5); ++k) s += red[k];
+        e_diag[w] = s;
+    }
+}
+
+__global__ void __launch_bounds__(VMC_THREADS)
+k_log_psi(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
+          const double *__restrict__ J, const uint16_t *occ_list, double *out, unsigned *status) {
+    const int w = blockIdx.x, ne = na + nb, N2 = 2 * M;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ double sm[];
+    __shared__ int s_so[2 * VMC_MAX_M];
+    __shared__ int s_piv;
+    __shared__ double red[VMC_WARPS];
+    const uint16_t *occ = occ_list + (size_t)w * ne;
+    for (int c = tid; c < ne; c += nt) s_so[c] = (c < na ? 0 : M) + occ[c];
+    __syncthreads();
+    // ln C[n] = sum_{p<q} J_pq n_p n_q + sum_p J_pp n_p over the occupied spin orbitals
+    double part = 0.0;
+    for (int t = tid; t < ne * ne; t += nt) {
+        const int x = t / ne, y = t % ne;
+        if (y < x) continue;
+        part += jget(J, N2, s_so[x], s_so[y]);
+    }
+    part = warp_sum_f64(part);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    double total = 0.0;
+    if (tid == 0)
+        for (int k = 0; k < (nt >> 5); ++k) total += red[k];
+    int sgn_total = 1;
+    for (int sg = 0; sg < 2; ++sg) {
+        const int n = sg ? nb : na;
+        if (n == 0) continue;
+        const double *C = sg ? Cb : Ca;
+        const int ld = n + 1;
+        __syncthreads();
+        for (int t = tid; t < n * n; t += nt) {
+            const int r = t / n, x = t % n;
+            sm[r * ld + x] = C[(size_t)occ[(sg ? na : 0) + r] * n + x];
+        }
+        __syncthreads();
+        double la;
+        int sgn;
+        lu_logdet(sm, n, ld, &s_piv, nullptr, &la, &sgn);
+        if (tid == 0) {
+            total += la;
+            sgn_total *= sgn;
+        }
+    }
+    if (tid == 0) {
+        if (sgn_total == 0) {
+            atomicOr(status, VMC_DEV_SINGULAR);
+            out[w] = -INFINITY;
+        } else {
+            out[w] = total;
+        }
+    }
+}
+
+}  // namespace
+
+vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, vmc_walkers *Wk,
+                               int full) {
+    const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
+    const int nmax = na > nb ? na : nb;
+    const size_t smem = sizeof(double) * ((size_t)2 * nmax * (nmax + 1) + nmax + 1);
+    if (smem > 227 * 1024) return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the in-SM inverse (max 118)");
+    vmc_status st = launch_refresh_jastrow(ctx, L, P->J);
+    if (st) return st;
+    dim3 grid(Wk->W, 2);
+    cudaError_t e;
+    if (Wk->precision == VMC_FP64) {
+        e = cudaFuncSetAttribute(k_init_tables<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_init_tables<double><<<grid, VMC_THREADS, smem, ctx->stream>>>(
+                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
+                (double *)Wk->G, (double *)Wk->AinvT, ctx->d_status);
+    } else {
+        e = cudaFuncSetAttribute(k_init_tables<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_init_tables<float><<<grid, VMC_THREADS, smem, ctx->stream>>>(
+                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
+                (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status);
+    }
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "k_init_tables");
+    if (Wk->precision == VMC_FP64)
+        k_init_sums<double><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
+            L->view, na, nb, P->J, Wk->occ_list, (double *)Wk->S, Wk->F, Wk->e_diag, full);
+    else
+        k_init_sums<float><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
+            L->view, na, nb, P->J, Wk->occ_list, (float *)Wk->S, Wk->F, Wk->e_diag, full);
+    ctx->launches += 1;
+    return cuda_check(ctx, cudaGetLastError(), "k_init_sums");
+}
+
+vmc_status launch_log_psi(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_params *P, double *out) {
+    const int nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
+    const size_t smem = sizeof(double) * ((size_t)nmax * (nmax + 1) + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_log_psi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        k_log_psi<<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(Wk->M, Wk->n_alpha, Wk->n_beta, P->C_alpha,
+                                                             P->C_beta, P->J, Wk->occ_list, out,
+                                                             ctx->d_status);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_check(ctx, e, "k_log_psi");
+}

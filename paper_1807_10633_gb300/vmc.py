@@ -1,0 +1,340 @@
+"""Python binding of the C ABI in include/vmc.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_build/libvmc.so``; nothing is computed in
+Python.  PyTorch provides device memory (tensors) and streams.  If the library has not been
+built the import of this module succeeds but every call raises ``RuntimeError``: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+VMC_FP64, VMC_MIXED = 0, 1
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SINGULAR", 5: "ERR_TIMEOUT",
+           6: "ERR_OVERFLOW", 7: "ERR_NOMOVE"}
+
+
+class VmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vmc {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vmc_walkers(ct.Structure):
+    _fields_ = [("W", ct.c_int), ("M", ct.c_int), ("n_alpha", ct.c_int), ("n_beta", ct.c_int),
+                ("precision", ct.c_int),
+                ("occ_bits", ct.c_void_p), ("occ_list", ct.c_void_p), ("virt_list", ct.c_void_p),
+                ("G", ct.c_void_p), ("AinvT", ct.c_void_p), ("S", ct.c_void_p), ("F", ct.c_void_p),
+                ("e_diag", ct.c_void_p), ("rng_counter", ct.c_void_p)]
+
+
+class vmc_params(ct.Structure):
+    _fields_ = [("J", ct.c_void_p), ("C_alpha", ct.c_void_p), ("C_beta", ct.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """The loaded CUDA library; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not LIB.exists():
+            raise RuntimeError(f"CUDA library {LIB} is not built; run __graft_entry__.build()")
+        L = ct.CDLL(str(LIB))
+        P, I, D, U64, I64 = ct.c_void_p, ct.c_int, ct.c_double, ct.c_uint64, ct.c_int64
+        sig = {
+            "vmc_create": ([ct.POINTER(P), I, P], I),
+            "vmc_destroy": ([P], I),
+            "vmc_set_stream": ([P, P], I),
+            "vmc_last_error": ([P], ct.c_char_p),
+            "vmc_sync": ([P], I),
+            "vmc_build_screened_lists": ([P, I, P, P, D, D, ct.POINTER(P)], I),
+            "vmc_lists_destroy": ([P], I),
+            "vmc_lists_info": ([P, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I64)], I),
+            "vmc_walkers_sizes": ([I, I, I, I, P, ct.POINTER(I64)], I),
+            "vmc_walkers_init": ([P, P, ct.POINTER(vmc_params), ct.POINTER(vmc_walkers)], I),
+            "vmc_walkers_refresh": ([P, P, ct.POINTER(vmc_params), ct.POINTER(vmc_walkers)], I),
+            "vmc_log_psi": ([P, ct.POINTER(vmc_walkers), ct.POINTER(vmc_params), P], I),
+            "vmc_local_energy": ([P, P, ct.POINTER(vmc_params), ct.POINTER(vmc_walkers), D, P, P], I),
+            "vmc_ctmc_step": ([P, P, ct.POINTER(vmc_params), ct.POINTER(vmc_walkers), U64, P], I),
+            "vmc_grad_logpsi": ([P, ct.POINTER(vmc_walkers), P, P, P, P], I),
+            "vmc_amsgrad_update": ([P, P, P, P, P, ct.c_size_t, D, D, D], I),
+            "vmc_walker_reduce": ([P, I, P, P, P], I),
+            "vmc_launch_count": ([P], U64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return t.ctypes.data
+    return int(t)
+
+
+def _check(ctx, st: int):
+    if st != 0:
+        msg = lib().vmc_last_error(ctx).decode() if ctx else ""
+        raise VmcError(st, msg)
+
+
+# ------------------------------------------------------------------ raw C-ABI wrappers
+def vmc_create(device: int = 0, stream=None):
+    ctx = ct.c_void_p()
+    s = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else (stream or 0)
+    _check(None, lib().vmc_create(ct.byref(ctx), device, s))
+    return ctx
+
+
+def vmc_destroy(ctx):
+    lib().vmc_destroy(ctx)
+
+
+def vmc_set_stream(ctx, stream):
+    s = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else (stream or 0)
+    _check(ctx, lib().vmc_set_stream(ctx, s))
+
+
+def vmc_last_error(ctx) -> str:
+    return lib().vmc_last_error(ctx).decode()
+
+
+def vmc_sync(ctx):
+    _check(ctx, lib().vmc_sync(ctx))
+
+
+def vmc_build_screened_lists(ctx, M: int, h1: np.ndarray, eri: np.ndarray, e_core: float, eps: float):
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    assert h1.size == M * M and eri.size == M ** 4
+    out = ct.c_void_p()
+    _check(ctx, lib().vmc_build_screened_lists(ctx, M, _ptr(h1), _ptr(eri), float(e_core), float(eps),
+                                               ct.byref(out)))
+    return out
+
+
+def vmc_lists_destroy(lists):
+    lib().vmc_lists_destroy(lists)
+
+
+def vmc_lists_info(lists):
+    a, b, c = ct.c_int64(), ct.c_int64(), ct.c_int64()
+    _check(None, lib().vmc_lists_info(lists, ct.byref(a), ct.byref(b), ct.byref(c)))
+    return a.value, b.value, c.value
+
+
+def vmc_walkers_sizes(W, M, na, nb, lists):
+    out = (ct.c_int64 * 9)()
+    _check(None, lib().vmc_walkers_sizes(W, M, na, nb, lists, out))
+    return list(out)
+
+
+def vmc_walkers_init(ctx, lists, params, walkers):
+    _check(ctx, lib().vmc_walkers_init(ctx, lists, ct.byref(params), ct.byref(walkers)))
+
+
+def vmc_walkers_refresh(ctx, lists, params, walkers):
+    _check(ctx, lib().vmc_walkers_refresh(ctx, lists, ct.byref(params), ct.byref(walkers)))
+
+
+def vmc_log_psi(ctx, walkers, params, out):
+    _check(ctx, lib().vmc_log_psi(ctx, ct.byref(walkers), ct.byref(params), _ptr(out)))
+
+
+def vmc_local_energy(ctx, lists, params, walkers, eps_run, e_loc, t_res):
+    _check(ctx, lib().vmc_local_energy(ctx, lists, ct.byref(params), ct.byref(walkers), float(eps_run),
+                                       _ptr(e_loc), _ptr(t_res)))
+
+
+def vmc_ctmc_step(ctx, lists, params, walkers, seed, move_code):
+    _check(ctx, lib().vmc_ctmc_step(ctx, lists, ct.byref(params), ct.byref(walkers), int(seed),
+                                    _ptr(move_code)))
+
+
+def vmc_grad_logpsi(ctx, walkers, w, dJ, dCa, dCb):
+    _check(ctx, lib().vmc_grad_logpsi(ctx, ct.byref(walkers), _ptr(w), _ptr(dJ), _ptr(dCa), _ptr(dCb)))
+
+
+def vmc_amsgrad_update(ctx, p, g, m, n, alpha, beta1, beta2):
+    _check(ctx, lib().vmc_amsgrad_update(ctx, _ptr(p), _ptr(g), _ptr(m), _ptr(n), p.numel(),
+                                         float(alpha), float(beta1), float(beta2)))
+
+
+def vmc_walker_reduce(ctx, W, t_res, e_loc, out):
+    _check(ctx, lib().vmc_walker_reduce(ctx, W, _ptr(t_res), _ptr(e_loc), _ptr(out)))
+
+
+def vmc_launch_count(ctx) -> int:
+    return int(lib().vmc_launch_count(ctx))
+
+
+# ------------------------------------------------------------------ device buffers
+@dataclass
+class Walkers:
+    """Caller-owned device arrays of the walker state (layout in include/vmc.h)."""
+    W: int
+    M: int
+    n_alpha: int
+    n_beta: int
+    precision: int
+    occ_bits: torch.Tensor
+    occ_list: torch.Tensor
+    virt_list: torch.Tensor
+    G: torch.Tensor
+    AinvT: torch.Tensor
+    S: torch.Tensor
+    F: torch.Tensor
+    e_diag: torch.Tensor
+    rng_counter: torch.Tensor
+
+    @classmethod
+    def allocate(cls, W, M, na, nb, lists, precision=VMC_FP64, device="cuda"):
+        n = vmc_walkers_sizes(W, M, na, nb, lists)
+        real = torch.float64 if precision == VMC_FP64 else torch.float32
+        z = lambda k, dt: torch.zeros(max(1, n[k]), dtype=dt, device=device)
+        return cls(W, M, na, nb, precision, z(0, torch.int32), z(1, torch.int16), z(2, torch.int16),
+                   z(3, real), z(4, real), z(5, real), z(6, torch.float64), z(7, torch.float64),
+                   z(8, torch.int64))
+
+    def struct(self) -> vmc_walkers:
+        return vmc_walkers(self.W, self.M, self.n_alpha, self.n_beta, self.precision,
+                           _ptr(self.occ_bits), _ptr(self.occ_list), _ptr(self.virt_list), _ptr(self.G),
+                           _ptr(self.AinvT), _ptr(self.S), _ptr(self.F), _ptr(self.e_diag),
+                           _ptr(self.rng_counter))
+
+
+def params_struct(J: torch.Tensor, Ca: torch.Tensor, Cb: torch.Tensor) -> vmc_params:
+    for t in (J, Ca, Cb):
+        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    return vmc_params(_ptr(J), _ptr(Ca), _ptr(Cb))
+
+
+def decode_moves(codes: np.ndarray) -> np.ndarray:
+    """uint64 move codes -> (W, 5) int array (kind, i, j, a, b); j = b = -1 for singles."""
+    c = codes.astype(np.uint64)
+    out = np.stack([(c & 3), (c >> 2) & 1023, (c >> 12) & 1023, (c >> 22) & 1023, (c >> 32) & 1023],
+                   axis=1).astype(np.int64)
+    single = out[:, 0] == 1
+    out[single, 2] = -1
+    out[single, 4] = -1
+    return out
+
+
+class Engine:
+    """One Hamiltonian, one parameter set and W walkers on one GPU (thin convenience wrapper)."""
+
+    def __init__(self, system, params, occ: np.ndarray, eps: float, precision: int = VMC_FP64,
+                 device: int = 0, stream=None):
+        self.device = torch.device("cuda", device)
+        self.M, self.na, self.nb = system.M, system.n_alpha, system.n_beta
+        self.eps = float(eps)
+        self.ctx = vmc_create(device, stream if stream is not None else torch.cuda.current_stream(device))
+        self.lists = vmc_build_screened_lists(self.ctx, system.M, system.h1, system.eri, system.e_core, eps)
+        self.J = torch.as_tensor(params.J, dtype=torch.float64, device=self.device).contiguous()
+        self.Ca = torch.as_tensor(params.C_alpha, dtype=torch.float64, device=self.device).contiguous()
+        self.Cb = torch.as_tensor(params.C_beta, dtype=torch.float64, device=self.device).contiguous()
+        self.W = occ.shape[0]
+        self.walkers = Walkers.allocate(self.W, self.M, self.na, self.nb, self.lists, precision, self.device)
+        self.walkers.occ_list.copy_(torch.from_numpy(occ.astype(np.int16).reshape(-1)))
+        self.e_loc = torch.zeros(self.W, dtype=torch.float64, device=self.device)
+        self.t_res = torch.zeros(self.W, dtype=torch.float64, device=self.device)
+        self.moves = torch.zeros(self.W, dtype=torch.int64, device=self.device)
+        self.init()
+
+    @property
+    def params(self) -> vmc_params:
+        return params_struct(self.J, self.Ca, self.Cb)
+
+    def init(self):
+        vmc_walkers_init(self.ctx, self.lists, self.params, self.walkers.struct())
+
+    def refresh(self):
+        vmc_walkers_refresh(self.ctx, self.lists, self.params, self.walkers.struct())
+
+    def local_energy(self, eps_run: float | None = None):
+        vmc_local_energy(self.ctx, self.lists, self.params, self.walkers.struct(),
+                         self.eps if eps_run is None else eps_run, self.e_loc, self.t_res)
+        return self.e_loc, self.t_res
+
+    def ctmc_step(self, seed: int):
+        vmc_ctmc_step(self.ctx, self.lists, self.params, self.walkers.struct(), seed, self.moves)
+        return self.moves
+
+    def grad_logpsi(self, w: torch.Tensor, dJ=None, dCa=None, dCb=None):
+        dJ = torch.zeros_like(self.J) if dJ is None else dJ
+        dCa = torch.zeros_like(self.Ca) if dCa is None else dCa
+        dCb = torch.zeros_like(self.Cb) if dCb is None else dCb
+        vmc_grad_logpsi(self.ctx, self.walkers.struct(), w.contiguous(), dJ, dCa, dCb)
+        return dJ, dCa, dCb
+
+    def log_psi(self) -> torch.Tensor:
+        out = torch.zeros(self.W, dtype=torch.float64, device=self.device)
+        vmc_log_psi(self.ctx, self.walkers.struct(), self.params, out)
+        return out
+
+    def sync(self):
+        vmc_sync(self.ctx)
+
+    def occupations(self) -> np.ndarray:
+        """(W, 2M) uint8 occupation numbers from the device bit strings."""
+        bits = self.walkers.occ_bits.cpu().numpy().view(np.uint32).reshape(self.W, 2, -1)
+        M = self.M
+        n = np.zeros((self.W, 2 * M), dtype=np.uint8)
+        for s in range(2):
+            for k in range(M):
+                n[:, s * M + k] = (bits[:, s, k // 32] >> np.uint32(k % 32)) & 1
+        return n
+
+    def close(self):
+        if getattr(self, "lists", None):
+            vmc_lists_destroy(self.lists)
+            self.lists = None
+        if getattr(self, "ctx", None):
+            vmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LogPsi(torch.autograd.Function):
+    """ln|psi(n_w)| per walker as a differentiable function of (J, C_alpha, C_beta).
+
+    forward: vmc_log_psi (FP64 LU per walker); backward: vmc_grad_logpsi, the hand-written
+    vector-Jacobian product of the gradient ratios of Sec. III.B.  J enters through its upper
+    triangle, so the lower triangle of dJ is zero.
+    """
+
+    @staticmethod
+    def forward(ctx, J, Ca, Cb, engine: Engine):
+        prm = params_struct(J.contiguous(), Ca.contiguous(), Cb.contiguous())
+        out = torch.zeros(engine.W, dtype=torch.float64, device=J.device)
+        vmc_log_psi(engine.ctx, engine.walkers.struct(), prm, out)
+        ctx.engine = engine
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        e = ctx.engine
+        dJ, dCa, dCb = e.grad_logpsi(grad_out.contiguous().to(torch.float64))
+        return dJ, dCa, dCb, None

@@ -1,0 +1,48 @@
+"""The C-ABI library builds, loads and exports every symbol include/vmc.h declares (CPU only)."""
+import ctypes as ct
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    text = (ROOT / "include" / "vmc.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vmc_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libvmc():
+    from paper_1807_10633_gb300 import build
+    return ct.CDLL(str(build.build()))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["vmc_build_screened_lists", "vmc_local_energy", "vmc_ctmc_step",
+                     "vmc_grad_logpsi", "vmc_amsgrad_update"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libvmc):
+    missing = [n for n in declared_functions() if not hasattr(libvmc, n)]
+    assert not missing, missing
+
+
+def test_binding_exposes_the_same_names():
+    from paper_1807_10633_gb300 import vmc
+    for n in declared_functions():
+        assert hasattr(vmc, n), n
+
+
+def test_null_arguments_are_rejected_without_a_gpu(libvmc):
+    libvmc.vmc_walkers_sizes.restype = ct.c_int
+    out = (ct.c_int64 * 9)()
+    assert libvmc.vmc_walkers_sizes(4, 0, 1, 1, None, out) == 1          # M < 1
+    assert libvmc.vmc_walkers_sizes(4, 10, 5, 5, None, out) == 0
+    assert list(out)[:3] == [4 * 2 * 1, 4 * 10, 4 * 10]
+    libvmc.vmc_lists_info.restype = ct.c_int
+    assert libvmc.vmc_lists_info(None, None, None, None) == 1
