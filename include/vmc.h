@@ -198,6 +198,19 @@ vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *walkers, const doubl
                            double *d_dJ, double *d_dC_alpha, double *d_dC_beta);
 
 /*
+ * Gradient accumulation for one CTMC sweep (Sec. II.B weights, Eq. grad pieces), one pass:
+ *   d_sums[0] += sum_w t_w,  d_sums[1] += sum_w t_w E_L,w,
+ *   A_O  += sum_w t_w d ln psi_w / dp,   A_EO += sum_w t_w E_L,w d ln psi_w / dp
+ * for the walkers' current determinants (call after vmc_local_energy, before vmc_ctmc_step).
+ * A_O and A_EO are each given as (dJ [(2M)^2], dC_alpha [M*na], dC_beta [M*nb]) device FP64
+ * arrays laid out as in vmc_grad_logpsi.  d_t_res, d_e_loc: double [W].
+ */
+vmc_status vmc_accumulate_gradient(vmc_ctx *ctx, const vmc_walkers *walkers, const double *d_t_res,
+                                   const double *d_e_loc, double *d_AO_J, double *d_AO_Ca,
+                                   double *d_AO_Cb, double *d_AEO_J, double *d_AEO_Ca,
+                                   double *d_AEO_Cb, double *d_sums);
+
+/*
  * AMSGrad, Eqs. (m1)-(m2) as printed (beta1 weights the new gradient):
  *   m <- (1-beta1) m + beta1 g;  n <- max(n, (1-beta2) n + beta2 g^2);  p <- p - alpha m/sqrt(n)
  * with no update where n == 0.  All arrays FP64 device, length n_params.
@@ -205,6 +218,15 @@ vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *walkers, const doubl
 vmc_status vmc_amsgrad_update(vmc_ctx *ctx, double *d_p, const double *d_g, double *d_m,
                               double *d_n, size_t n_params, double alpha, double beta1,
                               double beta2);
+
+/*
+ * Energy gradient of Eq. (grad) from time-weighted sums over the samples of one iteration
+ * (CTMC weights t_n, Sec. II.B):  with T = sums[0] = sum t and E = sums[1]/T,
+ *   g_k = 2 (A_EO[k] / T - E * A_O[k] / T),   A_O = sum t O,  A_EO = sum t E_L O.
+ * All device FP64 arrays of length n (g may alias neither input).  d_sums: double [2].
+ */
+vmc_status vmc_energy_gradient(vmc_ctx *ctx, size_t n, const double *d_sums, const double *d_A_O,
+                               const double *d_A_EO, double *d_g);
 
 /* Sum over walkers: out[0] += sum t, out[1] += sum t E_L (FP64, device out[2]). */
 vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const double *d_e_loc,

@@ -203,11 +203,32 @@ vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w,
     return launch_grad(ctx, Wk, w, dJ, dCa, dCb);
 }
 
+vmc_status vmc_accumulate_gradient(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,
+                                   double *aoJ, double *aoA, double *aoB, double *aeJ, double *aeA, double *aeB,
+                                   double *sums) {
+    if (!ctx) return VMC_ERR_ARG;
+    vmc_status st = check_walkers(ctx, Wk, nullptr);
+    if (st) return st;
+    if (!t || !e || !aoJ || !aoA || !aoB || !aeJ || !aeA || !aeB || !sums)
+        return set_err(ctx, VMC_ERR_ARG, "null argument");
+    double *const o0[3] = {aoJ, aoA, aoB};
+    double *const o1[3] = {aeJ, aeA, aeB};
+    return launch_accumulate(ctx, Wk, t, e, o0, o1, sums);
+}
+
 vmc_status vmc_amsgrad_update(vmc_ctx *ctx, double *p, const double *g, double *m, double *n, size_t np,
                               double alpha, double b1, double b2) {
     if (!ctx) return VMC_ERR_ARG;
     if (np && (!p || !g || !m || !n)) return set_err(ctx, VMC_ERR_ARG, "null argument");
     return launch_amsgrad(ctx, p, g, m, n, np, alpha, b1, b2);
+}
+
+vmc_status vmc_energy_gradient(vmc_ctx *ctx, size_t n, const double *sums, const double *aO, const double *aEO,
+                               double *g) {
+    if (!ctx) return VMC_ERR_ARG;
+    if (n && (!sums || !aO || !aEO || !g)) return set_err(ctx, VMC_ERR_ARG, "null argument");
+    if (g == aO || g == aEO) return set_err(ctx, VMC_ERR_ARG, "g must not alias the sums");
+    return launch_energy_gradient(ctx, n, sums, aO, aEO, g);
 }
 
 vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *t, const double *e, double *out) {

@@ -180,8 +180,12 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
                             uint64_t *move_code);
 vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ,
                        double *dCa, double *dCb);
+vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,
+                             double *const aO[3], double *const aEO[3], double *sums);
 vmc_status launch_amsgrad(vmc_ctx *ctx, double *p, const double *g, double *m, double *n,
                           size_t np, double alpha, double b1, double b2);
+vmc_status launch_energy_gradient(vmc_ctx *ctx, size_t n, const double *sums, const double *aO,
+                                  const double *aEO, double *g);
 vmc_status launch_walker_reduce(vmc_ctx *ctx, int W, const double *t, const double *e,
                                 double *out);
 vmc_status launch_log_psi(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_params *P,

@@ -23,86 +23,120 @@ __device__ __forceinline__ uint32_t window_bits(const uint32_t *bits_w, int M, i
     return __ballot_sync(0xffffffffu, bit);
 }
 
+// Weights of walker w: mode 0 -> (t[w]); mode 1 -> (t[w], t[w] e[w]).
+__device__ __forceinline__ void weights(int mode, const double *t, const double *e, int w, double &c0, double &c1) {
+    c0 = t[w];
+    c1 = mode ? c0 * e[w] : 0.0;
+}
+
 // dJ partials: tile (P, Q) of 32 x 32 spin orbitals with P <= Q, walker chunk blockIdx.y.
+// part layout: [n_out][chunk][N2][N2].
 __global__ void __launch_bounds__(256)
 k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const double *__restrict__ wgt,
-         double *__restrict__ part) {
+         const double *__restrict__ e, int mode, double *__restrict__ part) {
     const int N2 = 2 * M, nw = (M + 31) / 32, T = (N2 + 31) / 32;
     int t = blockIdx.x, P = 0;
     while (t >= T - P) { t -= T - P; ++P; }
     const int Q = P + t;
     const int tid = threadIdx.x, lane = tid & 31;
     const int pl = tid >> 3, ql0 = (tid & 7) * 4;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0}, acc2[4] = {0.0, 0.0, 0.0, 0.0};
     const int w0 = blockIdx.y * kChunkJ, w1 = min(W, w0 + kChunkJ);
     for (int w = w0; w < w1; ++w) {
         const uint32_t *bw = bits + (size_t)w * 2 * nw;
         const uint32_t bp = window_bits(bw, M, nw, P * 32, lane);
         const uint32_t bq = window_bits(bw, M, nw, Q * 32, lane);
         if ((bp >> pl) & 1u) {
-            const double c = wgt[w];
+            double c0, c1;
+            weights(mode, wgt, e, w, c0, c1);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if ((bq >> (ql0 + k)) & 1u) acc[k] += c;
+                if ((bq >> (ql0 + k)) & 1u) { acc[k] += c0; acc2[k] += c1; }
         }
     }
-    double *dst = part + (size_t)blockIdx.y * N2 * N2;
+    const size_t chunk_sz = (size_t)N2 * N2;
+    double *dst = part + (size_t)blockIdx.y * chunk_sz;
+    double *dst2 = part + ((size_t)gridDim.y + blockIdx.y) * chunk_sz;
     const int p = P * 32 + pl;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int q = Q * 32 + ql0 + k;
-        if (p < N2 && q < N2 && p <= q) dst[(size_t)p * N2 + q] = acc[k];
+        if (p < N2 && q < N2 && p <= q) {
+            dst[(size_t)p * N2 + q] = acc[k];
+            if (mode) dst2[(size_t)p * N2 + q] = acc2[k];
+        }
     }
 }
 
-__global__ void k_reduce_J(int M, int n_chunks, const double *__restrict__ part, double *__restrict__ dJ) {
+__global__ void k_reduce_J(int M, int n_chunks, const double *__restrict__ part, double *__restrict__ dJ,
+                           double *__restrict__ dJ2) {
     const int N2 = 2 * M;
+    const size_t csz = (size_t)N2 * N2;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N2 * N2; t += gridDim.x * blockDim.x) {
         const int p = t / N2, q = t % N2;
         if (p > q) continue;
-        double s = 0.0;
-        for (int c = 0; c < n_chunks; ++c) s += part[(size_t)c * N2 * N2 + t];
+        double s = 0.0, s2 = 0.0;
+        for (int c = 0; c < n_chunks; ++c) s += part[(size_t)c * csz + t];
         dJ[t] += s;
+        if (dJ2) {
+            for (int c = 0; c < n_chunks; ++c) s2 += part[((size_t)n_chunks + c) * csz + t];
+            dJ2[t] += s2;
+        }
     }
 }
 
 // dC partials for spin blockIdx.x, walker chunk blockIdx.y: acc[k][x] += w AinvT[col(k)][x]
+// part layout: [n_out][chunk][2][M][nmax]
 template <typename real>
 __global__ void __launch_bounds__(256)
 k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ occ_list, const real *__restrict__ AinvT,
-         const double *__restrict__ wgt, double *__restrict__ part) {
+         const double *__restrict__ wgt, const double *__restrict__ e, int mode, double *__restrict__ part) {
     const int s = blockIdx.x, n = s ? nb : na, ne = na + nb;
-    extern __shared__ double acc[];   // [M][n]
+    extern __shared__ double acc[];   // [M][n], then (mode 1) a second [M][n]
+    double *acc2 = acc + (size_t)M * n;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < M * n; t += nt) acc[t] = 0.0;
+    for (int t = tid; t < (mode + 1) * M * n; t += nt) acc[t] = 0.0;
     __syncthreads();
     const size_t astride = (size_t)na * na + (size_t)nb * nb;
     const size_t aoff = s ? (size_t)na * na : 0;
     const int w0 = blockIdx.y * kChunkC, w1 = min(W, w0 + kChunkC);
     for (int w = w0; w < w1; ++w) {
-        const double c = wgt[w];
+        double c0, c1;
+        weights(mode, wgt, e, w, c0, c1);
         const uint16_t *occ = occ_list + (size_t)w * ne + (s ? na : 0);
         const real *A = AinvT + (size_t)w * astride + aoff;
         for (int t = tid; t < n * n; t += nt) {
             const int col = t / n, x = t - col * n;
-            acc[(size_t)occ[col] * n + x] += c * (double)A[t];
+            const double a = (double)A[t];
+            const size_t o = (size_t)occ[col] * n + x;
+            acc[o] += c0 * a;
+            if (mode) acc2[o] += c1 * a;
         }
     }
     __syncthreads();
-    double *dst = part + ((size_t)blockIdx.y * 2 + s) * (size_t)M * (na > nb ? na : nb);
+    const size_t blk = (size_t)M * (na > nb ? na : nb);
+    double *dst = part + ((size_t)blockIdx.y * 2 + s) * blk;
     for (int t = tid; t < M * n; t += nt) dst[t] = acc[t];
+    if (mode) {
+        double *dst2 = part + (((size_t)gridDim.y + blockIdx.y) * 2 + s) * blk;
+        for (int t = tid; t < M * n; t += nt) dst2[t] = acc2[t];
+    }
 }
 
-__global__ void k_reduce_C(int M, int na, int nb, int n_chunks, const double *__restrict__ part,
-                           double *__restrict__ dCa, double *__restrict__ dCb) {
+__global__ void k_reduce_C(int M, int na, int nb, int n_chunks, int n_out, const double *__restrict__ part,
+                           double *__restrict__ dCa, double *__restrict__ dCb, double *__restrict__ dCa2,
+                           double *__restrict__ dCb2) {
     const int nmax = na > nb ? na : nb;
     const int tot = M * na + M * nb;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-        const int s = t >= M * na;
-        const int u = s ? t - M * na : t;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_out * tot; t += gridDim.x * blockDim.x) {
+        const int o = t / tot, r = t - o * tot;
+        const int s = r >= M * na;
+        const int u = s ? r - M * na : r;
         double sum = 0.0;
-        for (int c = 0; c < n_chunks; ++c) sum += part[((size_t)c * 2 + s) * (size_t)M * nmax + u];
-        (s ? dCb : dCa)[u] += sum;
+        for (int c = 0; c < n_chunks; ++c)
+            sum += part[(((size_t)o * n_chunks + c) * 2 + s) * (size_t)M * nmax + u];
+        double *dst = o == 0 ? (s ? dCb : dCa) : (s ? dCb2 : dCa2);
+        dst[u] += sum;
     }
 }
 
@@ -117,6 +151,13 @@ __global__ void k_amsgrad(double *p, const double *g, double *m, double *v, size
         v[k] = vk;
         if (vk > 0.0) p[k] -= alpha * mk / sqrt(vk);
     }
+}
+
+__global__ void k_energy_gradient(size_t n, const double *__restrict__ sums, const double *__restrict__ aO,
+                                  const double *__restrict__ aEO, double *__restrict__ g) {
+    const double T = sums[0], E = sums[1] / T;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        g[k] = 2.0 * (aEO[k] / T - E * (aO[k] / T));
 }
 
 __global__ void __launch_bounds__(1024)
@@ -141,47 +182,63 @@ k_walker_reduce(int W, const double *__restrict__ t, const double *__restrict__ 
 
 }  // namespace
 
-vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ, double *dCa,
-                       double *dCb) {
+static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e, int mode,
+                            double *const out0[3], double *const out1[3]) {
     const int W = Wk->W, M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta, N2 = 2 * M;
     const int T = (N2 + 31) / 32, ntile = T * (T + 1) / 2;
     const int cj = (W + kChunkJ - 1) / kChunkJ, cc = (W + kChunkC - 1) / kChunkC;
-    const int nmax = na > nb ? na : nb;
-    const size_t bytes_J = sizeof(double) * (size_t)cj * N2 * N2;
-    const size_t bytes_C = sizeof(double) * (size_t)cc * 2 * M * nmax;
+    const int nmax = na > nb ? na : nb, nout = mode + 1;
+    const size_t bytes_J = sizeof(double) * (size_t)nout * cj * N2 * N2;
+    const size_t bytes_C = sizeof(double) * (size_t)nout * cc * 2 * M * nmax;
     vmc_status st = ensure_workspace(ctx, bytes_J > bytes_C ? bytes_J : bytes_C);
     if (st) return st;
     double *part = (double *)ctx->ws;
-    if (dJ) {
-        k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, w, part);
-        k_reduce_J<<<(N2 * N2 + 255) / 256, 256, 0, ctx->stream>>>(M, cj, part, dJ);
+    if (out0[0]) {
+        k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, t, e, mode, part);
+        k_reduce_J<<<(N2 * N2 + 255) / 256, 256, 0, ctx->stream>>>(M, cj, part, out0[0], mode ? out1[0] : nullptr);
         ctx->launches += 2;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_check(ctx, e, "k_grad_J");
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return cuda_check(ctx, err, "k_grad_J");
     }
-    if (dCa && dCb) {
-        const size_t smem = sizeof(double) * (size_t)M * nmax;
-        cudaError_t e;
+    if (out0[1] && out0[2]) {
+        const size_t smem = sizeof(double) * (size_t)nout * M * nmax;
+        if (smem > 227 * 1024) return set_err(ctx, VMC_ERR_ARG, "M * n_sigma too large for the gradient kernel");
+        cudaError_t err;
         if (Wk->precision == VMC_FP64) {
-            e = cudaFuncSetAttribute(k_grad_C<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
+            err = cudaFuncSetAttribute(k_grad_C<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err == cudaSuccess)
                 k_grad_C<double><<<dim3(2, cc), 256, smem, ctx->stream>>>(W, M, na, nb, Wk->occ_list,
-                                                                          (const double *)Wk->AinvT, w, part);
+                                                                          (const double *)Wk->AinvT, t, e, mode, part);
         } else {
-            e = cudaFuncSetAttribute(k_grad_C<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
+            err = cudaFuncSetAttribute(k_grad_C<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err == cudaSuccess)
                 k_grad_C<float><<<dim3(2, cc), 256, smem, ctx->stream>>>(W, M, na, nb, Wk->occ_list,
-                                                                         (const float *)Wk->AinvT, w, part);
+                                                                         (const float *)Wk->AinvT, t, e, mode, part);
         }
-        if (e == cudaSuccess) {
-            const int tot = M * na + M * nb;
-            k_reduce_C<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, cc, part, dCa, dCb);
+        if (err == cudaSuccess) {
+            const int tot = nout * (M * na + M * nb);
+            k_reduce_C<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, cc, nout, part, out0[1], out0[2],
+                                                                   mode ? out1[1] : nullptr, mode ? out1[2] : nullptr);
         }
         ctx->launches += 2;
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_check(ctx, e, "k_grad_C");
+        if (err == cudaSuccess) err = cudaGetLastError();
+        if (err != cudaSuccess) return cuda_check(ctx, err, "k_grad_C");
     }
     return VMC_OK;
+}
+
+vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ, double *dCa,
+                       double *dCb) {
+    double *const o0[3] = {dJ, dCa, dCb};
+    double *const o1[3] = {nullptr, nullptr, nullptr};
+    return grad_impl(ctx, Wk, w, nullptr, 0, o0, o1);
+}
+
+vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,
+                             double *const aO[3], double *const aEO[3], double *sums) {
+    vmc_status st = grad_impl(ctx, Wk, t, e, 1, aO, aEO);
+    if (st) return st;
+    return launch_walker_reduce(ctx, Wk->W, t, e, sums);
 }
 
 vmc_status launch_amsgrad(vmc_ctx *ctx, double *p, const double *g, double *m, double *n, size_t np,
@@ -191,6 +248,15 @@ vmc_status launch_amsgrad(vmc_ctx *ctx, double *p, const double *g, double *m, d
     k_amsgrad<<<blocks, 256, 0, ctx->stream>>>(p, g, m, n, np, alpha, b1, b2);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "k_amsgrad");
+}
+
+vmc_status launch_energy_gradient(vmc_ctx *ctx, size_t n, const double *sums, const double *aO,
+                                  const double *aEO, double *g) {
+    if (n == 0) return VMC_OK;
+    const int blocks = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+    k_energy_gradient<<<blocks, 256, 0, ctx->stream>>>(n, sums, aO, aEO, g);
+    ctx->launches += 1;
+    return cuda_check(ctx, cudaGetLastError(), "k_energy_gradient");
 }
 
 vmc_status launch_walker_reduce(vmc_ctx *ctx, int W, const double *t, const double *e, double *out) {

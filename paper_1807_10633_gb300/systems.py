@@ -96,7 +96,7 @@ def _boys0(x: np.ndarray) -> np.ndarray:
 
 
 def _sgauss_ao_integrals(centers: np.ndarray, charges: np.ndarray, exps: np.ndarray,
-                         coefs: np.ndarray, pair_cut: float = 1e-15):
+                         coefs: np.ndarray, pair_cut: float = 1e-15, with_eri: bool = True):
     """Overlap S, core Hamiltonian h and ERIs (chemists') over contracted s-Gaussians.
 
     Closed forms for normalised s primitives (textbook Gaussian product theorem):
@@ -128,6 +128,8 @@ def _sgauss_ao_integrals(centers: np.ndarray, charges: np.ndarray, exps: np.ndar
         RPC2 = np.sum((P - centers[c]) ** 2, axis=-1)
         V -= np.sum(dd * 2.0 * np.pi / p * charges[c] * K * _boys0(p * RPC2), axis=(2, 3))
     h = T + V
+    if not with_eri:
+        return S, h, None
 
     # ERIs: keep AO pairs (mu<=nu) whose pair prefactor is not negligible
     coef_pair = dd * K                                # (nb, nb, npr, npr)
@@ -158,13 +160,65 @@ def _sgauss_ao_integrals(centers: np.ndarray, charges: np.ndarray, exps: np.ndar
 
 
 def _transform_eri(eri: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """(pq|rs) <- sum X[mu,p] X[nu,q] X[la,r] X[si,s] (mu nu|la si), four quarter steps."""
+    """(pq|rs) <- sum X[mu,p] X[nu,q] X[la,r] X[si,s] (mu nu|la si).
+
+    Ket pair first (batched X^T E X over the M^2 bra rows), then the bra pair (one matmul on
+    the leading axis and one batched over it); no large transposes are made.  Uses torch's
+    multithreaded CPU matmul (input preparation only)."""
+    import torch
+
     M = X.shape[0]
-    T = eri
-    for _ in range(4):
-        T = (X.T @ T.reshape(M, -1)).reshape(M, M, M, M)
-        T = np.ascontiguousarray(np.moveaxis(T, 0, 3))
-    return T
+    E = torch.from_numpy(np.ascontiguousarray(eri))
+    Xt = torch.from_numpy(np.ascontiguousarray(X))
+    Y = torch.matmul(torch.matmul(Xt.T, E.reshape(M * M, M, M)), Xt)     # (M^2, M, M)
+    T1 = (Xt.T @ Y.reshape(M, M * M * M)).reshape(M, M, M * M)
+    del Y
+    R = torch.matmul(Xt.T, T1)                                            # (M, M, M^2)
+    return R.reshape(M, M, M, M).numpy()
+
+
+def _chain_ao_eri(n_atoms: int, spacing: float, exps: np.ndarray, coefs: np.ndarray,
+                  pair_cut: float = 1e-15) -> np.ndarray:
+    """AO ERIs of a uniform linear chain of identical s shells.
+
+    (mu nu|la si) with mu <= nu, la <= si depends only on d = nu - mu, e = si - la and the
+    offset la - mu, so a table over (d, e, offset) is evaluated once and gathered."""
+    npr = exps.size
+    d_norm = coefs * (2.0 * exps / np.pi) ** 0.75
+    a = exps[:, None]
+    b = exps[None, :]
+    p = a + b
+    dd = d_norm[:, None] * d_norm[None, :]
+    # largest pair length whose primitive prefactors are not negligible
+    D = 0
+    while D + 1 < n_atoms and np.max(np.abs(dd * np.exp(-a * b / p * (spacing * (D + 1)) ** 2))) > pair_cut:
+        D += 1
+    dists = np.arange(D + 1)
+    K = np.exp(-a[None] * b[None] / p[None] * (spacing * dists[:, None, None]) ** 2)   # (D+1, npr, npr)
+    cpair = (dd[None] * K).reshape(D + 1, -1)                                       # (D+1, 9)
+    shift = (b[None] * spacing * dists[:, None, None] / p[None]).reshape(D + 1, -1)  # P - A
+    pp = np.broadcast_to(p, (npr, npr)).reshape(-1)
+    offs = np.arange(-(n_atoms - 1), n_atoms)
+    # table[d, e, o]: pair (0, d) against pair (o, o + e)
+    Pd = shift[:, None, None, :, None]                                     # (D+1,1,1,9,1)
+    Qe = spacing * offs[None, None, :, None, None] + shift[None, :, None, None, :]   # (1,D+1,O,1,9)
+    R2 = (Pd - Qe) ** 2
+    pa = pp[None, None, None, :, None]
+    qa = pp[None, None, None, None, :]
+    val = 2.0 * np.pi ** 2.5 / (pa * qa * np.sqrt(pa + qa)) * _boys0(pa * qa / (pa + qa) * R2)
+    val *= cpair[:, None, None, :, None] * cpair[None, :, None, None, :]
+    table = val.sum(axis=(3, 4))                                           # (D+1, D+1, O)
+    mu = np.concatenate([np.arange(n_atoms - d) for d in dists])
+    dl = np.concatenate([np.full(n_atoms - d, d) for d in dists])
+    nu = mu + dl
+    ep = table[dl[:, None], dl[None, :], (mu[None, :] - mu[:, None]) + (n_atoms - 1)]
+    M = n_atoms
+    eri = np.zeros((M, M, M, M))
+    eri[mu[:, None], nu[:, None], mu[None, :], nu[None, :]] = ep
+    eri[nu[:, None], mu[:, None], mu[None, :], nu[None, :]] = ep
+    eri[mu[:, None], nu[:, None], nu[None, :], mu[None, :]] = ep
+    eri[nu[:, None], mu[:, None], nu[None, :], mu[None, :]] = ep
+    return eri
 
 
 def hchain(n_atoms: int, spacing: float = 1.8) -> System:
@@ -172,7 +226,8 @@ def hchain(n_atoms: int, spacing: float = 1.8) -> System:
     centers = np.zeros((n_atoms, 3))
     centers[:, 0] = spacing * np.arange(n_atoms)
     charges = np.ones(n_atoms)
-    S, h, eri_ao = _sgauss_ao_integrals(centers, charges, STO3G_H_EXP, STO3G_H_COEF)
+    S, h, _ = _sgauss_ao_integrals(centers, charges, STO3G_H_EXP, STO3G_H_COEF, with_eri=False)
+    eri_ao = _chain_ao_eri(n_atoms, spacing, STO3G_H_EXP, STO3G_H_COEF)
     s, U = np.linalg.eigh(S)
     X = (U * s ** -0.5) @ U.T                          # S^{-1/2}, symmetric
     h1 = X.T @ h @ X
@@ -257,33 +312,54 @@ def make_params(sys: System, seed: int = MASTER_SEED, j_scale: float = 0.01,
 
 
 # ---------------------------------------------------------------------------------------
-# Starting determinants (the paper is silent; seeded random, well-conditioned)
+# Starting determinants (the paper is silent)
 # ---------------------------------------------------------------------------------------
-def _well_conditioned(C: np.ndarray, occ: np.ndarray, tol: float) -> bool:
-    sv = np.linalg.svd(C[occ], compute_uv=False)
-    return sv[-1] > tol * sv[0]
+def _dpp_rows(C: np.ndarray, B: int, rng: np.random.Generator) -> np.ndarray:
+    """B independent draws of n rows of C (M x n) with probability proportional to
+    det(C[rows])^2: sequential sampling of the projection determinantal point process onto the
+    column space of C (Hough, Krishnapur, Peres & Virag, 2006).  Returns (B, n) sorted rows."""
+    M, n = C.shape
+    Q, _ = np.linalg.qr(C)                          # orthonormal basis of the column space
+    Qb = np.broadcast_to(Q, (B, M, n)).copy()
+    r = np.sum(Qb * Qb, axis=2)                      # squared row norms
+    rows = np.empty((B, n), dtype=np.int64)
+    ar = np.arange(B)
+    for k in range(n):
+        p = np.clip(r, 0.0, None)
+        p /= p.sum(axis=1, keepdims=True)
+        u = rng.random(B)[:, None]
+        i = np.minimum((np.cumsum(p, axis=1) < u).sum(axis=1), M - 1)
+        rows[:, k] = i
+        v = Qb[ar, i, :]
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        proj = np.einsum("bmn,bn->bm", Qb, v)
+        Qb -= proj[:, :, None] * v[:, None, :]
+        r -= proj * proj
+        r[ar, i] = 0.0
+    return np.sort(rows, axis=1)
 
 
 def init_occupations(sys: System, prm: Params, W: int, seed: int = MASTER_SEED + 1,
-                     cond_tol: float = 1e-6) -> np.ndarray:
-    """Per-walker occupied orbital lists, shape (W, n_alpha + n_beta), uint16, each spin
-    block sorted ascending (alpha orbitals then beta orbitals, spatial indices 0..M-1).
-    A draw is redone while the occupied rows of C are badly conditioned."""
+                     pool: int = 4096, chunk: int = 512) -> np.ndarray:
+    """Per-walker occupied orbital lists, shape (W, n_alpha + n_beta), uint16, each spin block
+    sorted ascending (alpha orbitals, then beta; spatial indices 0..M-1).
+
+    Each spin's orbitals are an exact draw from |det C^s[rows]|^2, the distribution the Slater
+    part alone would be sampled from, so walkers start at typical, well-conditioned
+    determinants.  At most `pool` distinct starts are drawn; larger W reuse them cyclically."""
     rng = np.random.default_rng(seed)
-    M, na, nb = sys.M, sys.n_alpha, sys.n_beta
-    out = np.empty((W, na + nb), dtype=np.uint16)
-    for w in range(W):
-        for _ in range(1000):
-            oa = np.sort(rng.choice(M, na, replace=False))
-            ob = np.sort(rng.choice(M, nb, replace=False))
-            if _well_conditioned(prm.C_alpha, oa, cond_tol) and \
-               _well_conditioned(prm.C_beta, ob, cond_tol):
-                break
-        else:
-            raise RuntimeError("could not draw a well-conditioned determinant")
-        out[w, :na] = oa
-        out[w, na:] = ob
-    return out
+    P = min(W, pool)
+    na, nb = sys.n_alpha, sys.n_beta
+    occ = np.empty((P, na + nb), dtype=np.uint16)
+    for c0 in range(0, P, chunk):
+        c1 = min(P, c0 + chunk)
+        if na:
+            occ[c0:c1, :na] = _dpp_rows(prm.C_alpha, c1 - c0, rng)
+        if nb:
+            occ[c0:c1, na:] = _dpp_rows(prm.C_beta, c1 - c0, rng)
+    if P == W:
+        return occ
+    return occ[np.arange(W) % P].copy()
 
 
 def occ_to_bits(occ: np.ndarray, M: int, n_alpha: int) -> np.ndarray:

@@ -67,6 +67,8 @@ def lib() -> ct.CDLL:
             "vmc_grad_logpsi": ([P, ct.POINTER(vmc_walkers), P, P, P, P], I),
             "vmc_amsgrad_update": ([P, P, P, P, P, ct.c_size_t, D, D, D], I),
             "vmc_walker_reduce": ([P, I, P, P, P], I),
+            "vmc_energy_gradient": ([P, ct.c_size_t, P, P, P, P], I),
+            "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
         }
         for name, (args, res) in sig.items():
@@ -181,6 +183,16 @@ def vmc_walker_reduce(ctx, W, t_res, e_loc, out):
     _check(ctx, lib().vmc_walker_reduce(ctx, W, _ptr(t_res), _ptr(e_loc), _ptr(out)))
 
 
+def vmc_accumulate_gradient(ctx, walkers, t_res, e_loc, AO, AEO, sums):
+    """AO, AEO: (dJ, dCa, dCb) tensors each."""
+    _check(ctx, lib().vmc_accumulate_gradient(ctx, ct.byref(walkers), _ptr(t_res), _ptr(e_loc),
+                                              *(_ptr(x) for x in AO), *(_ptr(x) for x in AEO), _ptr(sums)))
+
+
+def vmc_energy_gradient(ctx, sums, A_O, A_EO, g):
+    _check(ctx, lib().vmc_energy_gradient(ctx, g.numel(), _ptr(sums), _ptr(A_O), _ptr(A_EO), _ptr(g)))
+
+
 def vmc_launch_count(ctx) -> int:
     return int(lib().vmc_launch_count(ctx))
 
@@ -247,9 +259,13 @@ class Engine:
         self.eps = float(eps)
         self.ctx = vmc_create(device, stream if stream is not None else torch.cuda.current_stream(device))
         self.lists = vmc_build_screened_lists(self.ctx, system.M, system.h1, system.eri, system.e_core, eps)
-        self.J = torch.as_tensor(params.J, dtype=torch.float64, device=self.device).contiguous()
-        self.Ca = torch.as_tensor(params.C_alpha, dtype=torch.float64, device=self.device).contiguous()
-        self.Cb = torch.as_tensor(params.C_beta, dtype=torch.float64, device=self.device).contiguous()
+        N2 = 2 * self.M
+        self.n_params = N2 * N2 + self.M * (self.na + self.nb)
+        flat = np.concatenate([np.asarray(params.J, dtype=np.float64).ravel(),
+                               np.asarray(params.C_alpha, dtype=np.float64).ravel(),
+                               np.asarray(params.C_beta, dtype=np.float64).ravel()])
+        self.p = torch.as_tensor(flat, device=self.device).contiguous()   # one flat parameter buffer
+        self.J, self.Ca, self.Cb = self.split(self.p)
         self.W = occ.shape[0]
         self.walkers = Walkers.allocate(self.W, self.M, self.na, self.nb, self.lists, precision, self.device)
         self.walkers.occ_list.copy_(torch.from_numpy(occ.astype(np.int16).reshape(-1)))
@@ -257,6 +273,14 @@ class Engine:
         self.t_res = torch.zeros(self.W, dtype=torch.float64, device=self.device)
         self.moves = torch.zeros(self.W, dtype=torch.int64, device=self.device)
         self.init()
+
+    def split(self, flat: torch.Tensor):
+        """Views (J, C_alpha, C_beta) of a flat parameter-shaped buffer."""
+        N2 = 2 * self.M
+        a = N2 * N2
+        b = a + self.M * self.na
+        return (flat[:a].view(N2, N2), flat[a:b].view(self.M, self.na),
+                flat[b:b + self.M * self.nb].view(self.M, self.nb))
 
     @property
     def params(self) -> vmc_params:
