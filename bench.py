@@ -172,6 +172,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
         if e2e:
             out_host[:np_].copy_(eng.p, non_blocking=True)
             out_host[np_:].copy_(sums, non_blocking=True)
+            stream.synchronize()                 # the host needs the result before its next step
+            p_host.copy_(out_host[:np_])
 
     def timed_loop(e2e: bool, it0: int):
         torch.cuda.synchronize()
