@@ -112,6 +112,7 @@ k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ occ_list, co
             acc[o] += c0 * a;
             if (mode) acc2[o] += c1 * a;
         }
+        __syncthreads();   // the next walker maps columns to different rows
     }
     __syncthreads();
     const size_t blk = (size_t)M * (na > nb ? na : nb);
