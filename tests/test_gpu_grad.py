@@ -118,11 +118,26 @@ def test_sherman_morrison_tables_equal_recomputed(vmc, precision, tol):
         eng.local_energy()
         eng.ctmc_step(77)
     eng.sync()
-    G1, A1, S1, F1, E1 = (x.clone() for x in (eng.walkers.G, eng.walkers.AinvT, eng.walkers.S,
-                                               eng.walkers.F, eng.walkers.e_diag))
-    eng.init()      # full recompute from the (moved) occupations
+    def g_by_orbital():
+        # G rows are virtual slots; a full recompute renumbers the slots, so compare by orbital
+        M, na, nb, W = sys_.M, sys_.n_alpha, sys_.n_beta, eng.W
+        G = eng.walkers.G.double().cpu().numpy().reshape(W, -1)
+        V = eng.walkers.virt_list.cpu().numpy().astype(np.int64).reshape(W, -1)
+        out = np.zeros((W, 2, M, max(na, nb)))
+        for w in range(W):
+            ga = G[w, :(M - na) * na].reshape(M - na, na)
+            gb = G[w, (M - na) * na:].reshape(M - nb, nb)
+            out[w, 0, V[w, :M - na], :na] = ga
+            out[w, 1, V[w, M - na:], :nb] = gb
+        return out
+
+    G1 = g_by_orbital()
+    A1, S1, F1, E1 = (x.clone() for x in (eng.walkers.AinvT, eng.walkers.S, eng.walkers.F, eng.walkers.e_diag))
+    eng.init()      # full recompute from the (moved) occupations, same column order
     eng.sync()
-    for a, b in [(G1, eng.walkers.G), (A1, eng.walkers.AinvT), (S1, eng.walkers.S)]:
+    G2 = g_by_orbital()
+    assert np.max(np.abs(G1 - G2)) <= tol * max(1.0, np.abs(G2).max())
+    for a, b in [(A1, eng.walkers.AinvT), (S1, eng.walkers.S)]:
         a = a.double().cpu().numpy(); b = b.double().cpu().numpy()
         assert np.max(np.abs(a - b)) <= tol * max(1.0, np.abs(b).max())
     assert np.max(np.abs(F1.cpu().numpy() - eng.walkers.F.cpu().numpy())) < 1e-11
