@@ -168,7 +168,7 @@ vmc_status vmc_local_energy(vmc_ctx *ctx, const vmc_lists *Lc, const vmc_params 
     if (!(eps_run >= L->eps_build)) return set_err(ctx, VMC_ERR_ARG, "eps_run must be >= the build eps");
     st = lists_set_eps(ctx, L, eps_run);
     if (st) return st;
-    const int ng = num_groups(Wk->n_alpha + Wk->n_beta);
+    const int ng = L->view.n_groups;
     void *rates = nullptr;
     st = ensure_rates(ctx, sizeof(u128) * (size_t)ng * Wk->W, &rates);
     if (st) return st;

@@ -39,6 +39,9 @@ struct vmc_ctx {
 // Plain-pointer view of the device lists, passed to kernels by value.
 struct ListsView {
     int M;
+    int band;      // largest |p - q| with a non-empty double list (pair candidates of a row)
+    int cpr;       // warp chunks (32 candidates) per spin-orbital row
+    int n_groups;  // singles blocks of 32 spin orbitals + 2M * cpr row chunks
     int64_t ns, nds, ndo;
     // singles, CSR over spatial i
     const uint32_t *s_off, *s_len, *s_owner;
@@ -167,7 +170,6 @@ vmc_status cuda_check(vmc_ctx *ctx, cudaError_t e, const char *what);
 vmc_status ensure_workspace(vmc_ctx *ctx, size_t bytes);
 size_t walker_stride_G(int M, int na, int nb);
 size_t walker_stride_A(int na, int nb);
-int num_groups(int ne);
 
 // launchers (defined in the .cu files)
 vmc_status launch_refresh_jastrow(vmc_ctx *ctx, vmc_lists *L, const double *J);

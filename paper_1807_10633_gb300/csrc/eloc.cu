@@ -2,13 +2,17 @@
 //
 // One CTA per walker.  The walker's G (virtual rows only), exp(S) and the orbital -> column /
 // slot map are staged in shared memory; the screened lists (shared by all walkers, L2-resident)
-// are streamed per occupied pair.  Work units in canonical order are: the walker's occupied spin
-// orbitals (singles), then its occupied pairs (i<j) lexicographically (doubles).  Units are taken
-// 32 at a time ("groups"); inside a group the lists of the 32 units are concatenated and walked
-// one entry per lane, so short lists do not idle lanes.  Each group's CTMC rates are summed as
+// are streamed per occupied pair.  Work is split into "groups" in canonical move order:
+//   singles : blocks of 32 consecutive spin orbitals i; unit = occupied i, list = singles(i)
+//   doubles : one group per spin-orbital row i (warp chunks of 32 candidates if needed); the
+//             candidates j > i of a row are the spin orbitals whose spatial index lies within
+//             the band of non-empty pair lists (same spin: q in (p, p+B]; alpha rows also
+//             opposite spin q in [p-B, p+B]), so a row fits one warp for local orbitals.
+// A warp takes one group; its active units (i and j occupied, list non-empty) are walked in
+// order with the lanes over each unit's list entries.  Each group's CTMC rates are summed as
 // exact 128-bit fixed-point integers (order independent) and stored; the CTMC kernel re-walks
-// only the chosen group.  Every product that enters a rate uses explicitly rounded intrinsics so
-// the two kernels compute bit-identical rates.
+// only the chosen group.  Every product that enters a rate uses explicitly rounded intrinsics
+// so the two kernels compute bit-identical rates.
 #include <math.h>
 
 #include "common.cuh"
@@ -89,35 +93,76 @@ struct View {
     const double *F;       // walker F [2][ns]
     Geo geo;
     __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }
+    __device__ bool occ(int p) const { return !(pos[p] & 0x8000); }
 };
 
+// Candidate j of spin-orbital row i, t-th in ascending order (t < row_ncand).
+__device__ __forceinline__ int row_ncand(const ListsView &L, int i) {
+    const int M = L.M, s = i >= M, p = i - s * M;
+    const int nS = min(L.band, M - 1 - p);
+    if (s) return nS;
+    return nS + (min(M - 1, p + L.band) - max(0, p - L.band) + 1);
+}
+__device__ __forceinline__ int row_cand(const ListsView &L, int i, int t) {
+    const int M = L.M, s = i >= M, p = i - s * M;
+    const int nS = min(L.band, M - 1 - p);
+    if (t < nS) return i + 1 + t;
+    return M + max(0, p - L.band) + (t - nS);
+}
+
+// Set up the unit of lane `lane` in group g.  Returns false if the lane has no active unit.
 template <typename real>
-__device__ __forceinline__ void setup_unit(const ListsView &L, const View<real> &V, int kind_grp,
-                                           int x, int y, const uint16_t *socc, Unit<real> &u) {
-    const int M = V.geo.M;
-    if (kind_grp == 0) {
-        const int i = socc[y];
+__device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> &V, int g, int lane,
+                                           Unit<real> &u) {
+    const int M = L.M, Gs = (2 * M + 31) / 32;
+    u.len = 0;
+    if (g < Gs) {
+        const int i = g * 32 + lane;
+        if (i >= 2 * M || !V.occ(i)) return false;
         const int s = i >= M, pi = i - s * M;
         u.kind = 0; u.cls = s; u.i = i; u.j = -1;
         u.base = L.s_off[pi]; u.len = L.s_len[pi];
         u.ci = V.pos[i]; u.cj = 0;
         u.einv = rrcp(V.Ev(i));
-    } else {
-        const int i = socc[x], j = socc[y];
-        const int si = i >= M, sj = j >= M, pi = i - si * M, pj = j - sj * M;
-        u.i = i; u.j = j;
-        u.ci = V.pos[i]; u.cj = V.pos[j];
-        u.einv = rrcp(rmul(V.Ev(i), V.Ev(j)));
-        if (si == sj) {
-            const int t = tri_index(pi, pj, M);
-            u.kind = 1; u.cls = si;
-            u.base = L.ds_off[t]; u.len = L.ds_len[t];
-        } else {
-            const int t = pi * M + pj;
-            u.kind = 2; u.cls = 0;
-            u.base = L.do_off[t]; u.len = L.do_len[t];
-        }
+        return u.len > 0;
     }
+    const int r = (g - Gs) / L.cpr, chunk = (g - Gs) - r * L.cpr;
+    const int i = r;
+    if (!V.occ(i)) return false;
+    const int t = chunk * 32 + lane;
+    if (t >= row_ncand(L, i)) return false;
+    const int j = row_cand(L, i, t);
+    if (!V.occ(j)) return false;
+    const int si = i >= M, sj = j >= M, pi = i - si * M, pj = j - sj * M;
+    u.i = i; u.j = j;
+    u.ci = V.pos[i]; u.cj = V.pos[j];
+    if (si == sj) {
+        const int tt = tri_index(pi, pj, M);
+        u.kind = 1; u.cls = si;
+        u.base = L.ds_off[tt]; u.len = L.ds_len[tt];
+    } else {
+        const int tt = pi * M + pj;
+        u.kind = 2; u.cls = 0;
+        u.base = L.do_off[tt]; u.len = L.do_len[tt];
+    }
+    if (u.len == 0) return false;
+    u.einv = rrcp(rmul(V.Ev(i), V.Ev(j)));
+    return true;
+}
+
+template <typename real>
+__device__ __forceinline__ Unit<real> shfl_unit(const Unit<real> &u, int src) {
+    Unit<real> v;
+    v.base = __shfl_sync(0xffffffffu, u.base, src);
+    v.len = __shfl_sync(0xffffffffu, u.len, src);
+    v.kind = __shfl_sync(0xffffffffu, u.kind, src);
+    v.cls = __shfl_sync(0xffffffffu, u.cls, src);
+    v.ci = __shfl_sync(0xffffffffu, u.ci, src);
+    v.cj = __shfl_sync(0xffffffffu, u.cj, src);
+    v.i = __shfl_sync(0xffffffffu, u.i, src);
+    v.j = __shfl_sync(0xffffffffu, u.j, src);
+    v.einv = __shfl_sync(0xffffffffu, u.einv, src);
+    return v;
 }
 
 // Evaluate list entry `idx` of unit u.  Returns false if the target orbital(s) are occupied.
@@ -180,26 +225,8 @@ __device__ __forceinline__ u128 rate_of(real ratio, unsigned *flag) {
     return rate_fixed(r);
 }
 
-// Number of groups and the start of each row x of the doubles groups.
-__host__ __device__ inline int chunks_of_row(int ne, int x) { return (ne - 1 - x + 31) / 32; }
-
-// Decode group g -> (kind_grp, x, y0).  gstart[x] = first doubles group of row x.
-__device__ __forceinline__ void decode_group(int g, int ne, const uint16_t *gstart, int &kg, int &x, int &y0) {
-    const int gs = (ne + 31) / 32;
-    if (g < gs) { kg = 0; x = -1; y0 = g * 32; return; }
-    const int gd = g - gs;
-    int lo = 0, hi = ne - 2;   // largest x with gstart[x] <= gd
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (gstart[mid] <= gd) lo = mid; else hi = mid - 1;
-    }
-    kg = 1; x = lo; y0 = x + 1 + 32 * (gd - gstart[x]);
-}
-
-// Prologue shared by both kernels: orbital -> column/slot map, sorted occupied spin orbitals,
-// group row starts.
-__device__ void build_maps(const Geo &geo, const uint16_t *occ, const uint16_t *virt, const uint32_t *bits,
-                           uint16_t *pos, uint16_t *socc, uint16_t *gstart) {
+// Orbital -> column / virtual-slot map of one walker.
+__device__ void build_pos(const Geo &geo, const uint16_t *occ, const uint16_t *virt, uint16_t *pos) {
     const int tid = threadIdx.x, nt = blockDim.x, M = geo.M;
     for (int c = tid; c < geo.ne; c += nt) {
         const int s = c < geo.na ? 0 : 1;
@@ -212,20 +239,6 @@ __device__ void build_maps(const Geo &geo, const uint16_t *occ, const uint16_t *
         const int slot = t - (s ? geo.nv_a : 0);
         pos[s * M + virt[t]] = (uint16_t)(0x8000 | slot);
     }
-    // rank of each occupied spin orbital among all occupied spin orbitals (alpha block first)
-    for (int p = tid; p < 2 * M; p += nt) {
-        const int s = p >= M, k = p - s * M;
-        const uint32_t *bw = bits + s * geo.nw;
-        if (!((bw[k >> 5] >> (k & 31)) & 1u)) continue;
-        int r = s ? geo.na : 0;
-        for (int q = 0; q < (k >> 5); ++q) r += __popc(bw[q]);
-        r += __popc(bw[k >> 5] & ((1u << (k & 31)) - 1u));
-        socc[r] = (uint16_t)p;
-    }
-    if (tid == 0) {
-        int acc = 0;
-        for (int x = 0; x + 1 < geo.ne; ++x) { gstart[x] = (uint16_t)acc; acc += chunks_of_row(geo.ne, x); }
-    }
 }
 
 template <typename real> struct AccT { typedef double type; };
@@ -234,25 +247,18 @@ template <> struct AccT<float> { typedef float type; };
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
-               u128 *__restrict__ rates, int n_groups, unsigned *status) {
+               u128 *__restrict__ rates, unsigned *status) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    const int M = geo.M, ne = geo.ne;
+    const int M = geo.M, ne = geo.ne, n_groups = L.n_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
     real *sG = (real *)smraw;
     real *sE = sG + geo.g_stride;
     uint16_t *pos = (uint16_t *)(sE + 2 * M);
-    uint16_t *socc = pos + 2 * M;
-    uint16_t *gstart = socc + ne;
-    // per-warp unit tables
-    __shared__ uint32_t u_base[VMC_WARPS][32], u_off[VMC_WARPS][33];
-    __shared__ uint8_t u_kind[VMC_WARPS][32], u_cls[VMC_WARPS][32];
-    __shared__ uint16_t u_ci[VMC_WARPS][32], u_cj[VMC_WARPS][32];
-    __shared__ real u_einv[VMC_WARPS][32];
     __shared__ double red_e[VMC_WARPS];
     __shared__ u128 red_q[VMC_WARPS];
 
-    // ---- prologue: stage G (vectorised), exp(S), maps
+    // ---- prologue: stage G (vectorised), exp(S), orbital map
     {
         const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
         const size_t nbytes = geo.g_stride * sizeof(real);
@@ -267,8 +273,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
         }
         const real *Sw = (const real *)A.S + (size_t)w * 2 * M;
         for (int p = tid; p < 2 * M; p += nt) sE[p] = rexp(Sw[p]);
-        build_maps(geo, A.occ_list + (size_t)w * ne, A.virt_list + (size_t)w * (2 * M - ne),
-                   A.occ_bits + (size_t)w * 2 * geo.nw, pos, socc, gstart);
+        build_pos(geo, A.occ_list + (size_t)w * ne, A.virt_list + (size_t)w * (2 * M - ne), pos);
     }
     __syncthreads();
 
@@ -280,55 +285,28 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
     unsigned flag = 0;
 
     for (int g = warp; g < n_groups; g += VMC_WARPS) {
-        int kg, x, y0;
-        decode_group(g, ne, gstart, kg, x, y0);
-        const int y = y0 + lane;
         Unit<real> u;
-        u.len = 0;
-        if (y < ne) {
-            setup_unit<real>(L, V, kg, x, y, socc, u);
-            u_base[warp][lane] = u.base;
-            u_kind[warp][lane] = (uint8_t)u.kind;
-            u_cls[warp][lane] = (uint8_t)u.cls;
-            u_ci[warp][lane] = (uint16_t)u.ci;
-            u_cj[warp][lane] = (uint16_t)u.cj;
-            u_einv[warp][lane] = u.einv;
-        }
-        // exclusive scan of the list lengths
-        uint32_t incl = u.len;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += o;
-        }
-        u_off[warp][lane] = incl - u.len;
-        if (lane == 31) u_off[warp][32] = incl;
-        __syncwarp();
-        const uint32_t total = u_off[warp][32];
+        const bool act = setup_unit<real>(L, V, g, lane, u);
+        unsigned mask = __ballot_sync(0xffffffffu, act);
         acc_t e_grp = 0;
         u128 q_grp = 0;
-        for (uint32_t e = lane; e < total; e += 32) {
-            int lo = 0, hi = 31;   // owner: largest unit with u_off <= e
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (u_off[warp][mid] <= e) lo = mid; else hi = mid - 1;
-            }
-            Unit<real> v;
-            v.kind = u_kind[warp][lo]; v.cls = u_cls[warp][lo];
-            v.ci = u_ci[warp][lo]; v.cj = u_cj[warp][lo]; v.einv = u_einv[warp][lo];
-            const uint32_t idx = u_base[warp][lo] + (e - u_off[warp][lo]);
-            real ratio, contrib;
-            int a, b;
-            if (eval_entry<real>(L, V, v, idx, ratio, contrib, a, b)) {
-                e_grp += (acc_t)contrib;
-                q_grp += rate_of<real>(ratio, &flag);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const Unit<real> v = shfl_unit(u, src);
+            for (uint32_t k = lane; k < v.len; k += 32) {
+                real ratio, contrib;
+                int a, b;
+                if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) {
+                    e_grp += (acc_t)contrib;
+                    q_grp += rate_of<real>(ratio, &flag);
+                }
             }
         }
         e_acc += (double)e_grp;
         q_grp = warp_sum_u128(q_grp);
         if (lane == 0) rates[(size_t)w * n_groups + g] = q_grp;
         q_tot += q_grp;
-        __syncwarp();
     }
     e_acc = warp_sum_f64(e_acc);
     if (lane == 0) { red_e[warp] = e_acc; red_q[warp] = q_tot; }
@@ -353,18 +331,15 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 *__restrict__ rates,
-            int n_groups, uint64_t seed, uint64_t *__restrict__ move_code, unsigned *status) {
+            uint64_t seed, uint64_t *__restrict__ move_code, unsigned *status) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    const int M = geo.M, ne = geo.ne, N2 = 2 * M;
+    const int M = geo.M, ne = geo.ne, N2 = 2 * M, n_groups = L.n_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
     uint16_t *pos = (uint16_t *)smraw;
-    uint16_t *socc = pos + 2 * M;
-    uint16_t *gstart = socc + ne;
-    real *vec = (real *)(((uintptr_t)(gstart + ne) + 15) & ~(uintptr_t)15);
+    real *vec = (real *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15);
     // vec holds: ua[nmax], ub[nmax], gci[M], gcj[M], arow_i[nmax], arow_j[nmax]
     __shared__ int s_move[6];       // kind, i, j, a, b, ok
-    __shared__ uint32_t u_off[33];
     __shared__ double red[VMC_WARPS];
 
     real *Gw = (real *)A.G + (size_t)w * geo.g_stride;
@@ -373,7 +348,7 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
     uint16_t *occ = A.occ_list + (size_t)w * ne;
     uint16_t *virt = A.virt_list + (size_t)w * (2 * M - ne);
     uint32_t *bits = A.occ_bits_w + (size_t)w * 2 * geo.nw;
-    build_maps(geo, occ, virt, bits, pos, socc, gstart);
+    build_pos(geo, occ, virt, pos);
     __syncthreads();
 
     // ---- choose the group (warp 0), then the entry inside it
@@ -409,64 +384,36 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
             const u128 Tl = T - before;   // threshold inside the group
             View<real> V;
             V.pos = pos; V.G = Gw; V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
-            int kg, x, y0;
-            decode_group(gsel, ne, gstart, kg, x, y0);
-            const int y = y0 + lane;
             Unit<real> u;
-            u.base = 0; u.len = 0; u.kind = 0; u.cls = 0; u.ci = 0; u.cj = 0; u.i = 0; u.j = 0;
-            u.einv = (real)0;
-            if (y < ne) setup_unit<real>(L, V, kg, x, y, socc, u);
-            uint32_t inc = u.len;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-                if (lane >= d) inc += o;
-            }
-            u_off[lane] = inc - u.len;
-            if (lane == 31) u_off[32] = inc;
-            __syncwarp();
-            const uint32_t total = u_off[32];
+            const bool act = setup_unit<real>(L, V, gsel, lane, u);
+            unsigned mask = __ballot_sync(0xffffffffu, act);
             u128 carry = 0;
             unsigned flag = 0;
             bool found = false;
-            for (uint32_t e0 = 0; e0 < total && !found; e0 += 32) {
-                const uint32_t e = e0 + lane;
-                u128 q = 0;
-                int a = -1, b = -1, owner = 0;
-                if (e < total) {
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (u_off[mid] <= e) lo = mid; else hi = mid - 1;
+            while (mask && !found) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const Unit<real> v = shfl_unit(u, src);
+                for (uint32_t k0 = 0; k0 < v.len && !found; k0 += 32) {
+                    const uint32_t k = k0 + lane;
+                    u128 q = 0;
+                    int a = -1, b = -1;
+                    if (k < v.len) {
+                        real ratio, contrib;
+                        if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
                     }
-                    owner = lo;
-                }
-                // fetch the owner's unit fields by shuffles (all lanes participate)
-                Unit<real> v;
-                v.kind = __shfl_sync(0xffffffffu, u.kind, owner);
-                v.cls = __shfl_sync(0xffffffffu, u.cls, owner);
-                v.ci = __shfl_sync(0xffffffffu, u.ci, owner);
-                v.cj = __shfl_sync(0xffffffffu, u.cj, owner);
-                v.einv = __shfl_sync(0xffffffffu, u.einv, owner);
-                const uint32_t vbase = __shfl_sync(0xffffffffu, u.base, owner);
-                const int vi = __shfl_sync(0xffffffffu, u.i, owner);
-                const int vj = __shfl_sync(0xffffffffu, u.j, owner);
-                if (e < total) {
-                    real ratio, contrib;
-                    const uint32_t idx = vbase + (e - u_off[owner]);
-                    if (eval_entry<real>(L, V, v, idx, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
-                }
-                const u128 incl2 = warp_incl_scan_u128(q, lane) + carry;
-                const unsigned hit = __ballot_sync(0xffffffffu, e < total && incl2 > Tl);
-                if (hit) {
-                    const int src = __ffs(hit) - 1;
-                    if (lane == src) {
-                        s_move[0] = v.kind == 0 ? 1 : 2;
-                        s_move[1] = vi; s_move[2] = vj; s_move[3] = a; s_move[4] = b; s_move[5] = 1;
+                    const u128 incl2 = warp_incl_scan_u128(q, lane) + carry;
+                    const unsigned hit = __ballot_sync(0xffffffffu, k < v.len && q != 0 && incl2 > Tl);
+                    if (hit) {
+                        const int h = __ffs(hit) - 1;
+                        if (lane == h) {
+                            s_move[0] = v.kind == 0 ? 1 : 2;
+                            s_move[1] = v.i; s_move[2] = v.j; s_move[3] = a; s_move[4] = b; s_move[5] = 1;
+                        }
+                        found = true;
                     }
-                    found = true;
+                    carry = shfl_u128(incl2, 31);
                 }
-                carry = shfl_u128(incl2, 31);
             }
             if (!found && lane == 0) atomicOr(status, VMC_DEV_INCONSISTENT);
         } else if (lane == 0) {
@@ -485,7 +432,7 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
         move_code[w] = (uint64_t)kind | ((uint64_t)I << 2) | (j10 << 12) | ((uint64_t)Ao << 22) | (b10 << 32);
     }
 
-    // ---- diagonal energy change (old occupation in socc), FP64
+    // ---- diagonal energy change (old occupation), FP64
     {
         auto D = [&](int p, int q) -> double {
             const int kp = p % M, kq = q % M;
@@ -495,7 +442,7 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
         };
         double part = 0.0;
         for (int t = tid; t < ne; t += nt) {
-            const int K = socc[t];
+            const int K = (t < geo.na ? 0 : M) + occ[t];
             if (K != I) part += D(Ao, K) - D(I, K);
             if (kind == 2 && K != I && K != Jo) part += D(Bo, K) - D(Jo, K);
         }
@@ -613,12 +560,6 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
 
 }  // namespace
 
-int num_groups(int ne) {
-    int g = (ne + 31) / 32;
-    for (int x = 0; x + 1 < ne; ++x) g += chunks_of_row(ne, x);
-    return g;
-}
-
 static WalkerArgs make_args(vmc_walkers *Wk) {
     WalkerArgs A;
     A.W = Wk->W; A.M = Wk->M; A.na = Wk->n_alpha; A.nb = Wk->n_beta;
@@ -631,10 +572,11 @@ static WalkerArgs make_args(vmc_walkers *Wk) {
 
 vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk, double *e_loc,
                                double *t_res, u128 *rates, int n_groups) {
-    const int M = Wk->M, ne = Wk->n_alpha + Wk->n_beta;
+    const int M = Wk->M;
+    (void)n_groups;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const size_t gst = walker_stride_G(M, Wk->n_alpha, Wk->n_beta);
-    const size_t smem = esz * (gst + 2 * (size_t)M) + 2 * (2 * (size_t)M + 2 * (size_t)ne) + 16;
+    const size_t smem = esz * (gst + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e;
@@ -642,12 +584,12 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
         e = cudaFuncSetAttribute(k_local_energy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             k_local_energy<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                              n_groups, ctx->d_status);
+                                                                              ctx->d_status);
     } else {
         e = cudaFuncSetAttribute(k_local_energy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             k_local_energy<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                             n_groups, ctx->d_status);
+                                                                             ctx->d_status);
     }
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -656,21 +598,22 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
 
 vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, vmc_walkers *Wk,
                             uint64_t seed, const u128 *rates, int n_groups, uint64_t *move_code) {
-    const int M = Wk->M, ne = Wk->n_alpha + Wk->n_beta;
+    const int M = Wk->M;
+    (void)n_groups;
     const int nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
-    const size_t smem = 2 * (2 * (size_t)M + 2 * (size_t)ne) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
+    const size_t smem = 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
     WalkerArgs A = make_args(Wk);
     cudaError_t e;
     if (Wk->precision == VMC_FP64) {
         e = cudaFuncSetAttribute(k_ctmc_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_ctmc_step<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, n_groups, seed,
+            k_ctmc_step<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, seed,
                                                                            move_code, ctx->d_status);
     } else {
         e = cudaFuncSetAttribute(k_ctmc_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_ctmc_step<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, n_groups, seed,
+            k_ctmc_step<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, seed,
                                                                           move_code, ctx->d_status);
     }
     ctx->launches += 1;

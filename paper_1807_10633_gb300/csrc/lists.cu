@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "common.cuh"
@@ -250,6 +251,23 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     auto P = [&](size_t idx) { return (void *)(base + pcs[idx].off); };
     ListsView &v = L->view;
     v.M = M; v.ns = ns; v.nds = nds; v.ndo = ndo; v.e_core = e_core;
+    {
+        int band = 0;
+        for (int t = 0; t < npair; ++t)
+            if (!dl[t].empty()) {
+                int p = 0;
+                while (tri_index(p, M - 1, M) < t) ++p;
+                const int q = t - tri_index(p, p + 1, M) + p + 1;
+                band = std::max(band, q - p);
+            }
+        for (size_t t = 0; t < MM * MM; ++t)
+            if (!ol[t].empty()) band = std::max(band, std::abs((int)(t / M) - (int)(t % M)));
+        // candidates of an alpha row: same-spin q in (p, p+band], opposite q in [p-band, p+band]
+        const int cand = std::min(band, M - 1) + std::min(2 * band + 1, M);
+        v.band = band;
+        v.cpr = std::max(1, (cand + 31) / 32);
+        v.n_groups = (2 * M + 31) / 32 + 2 * M * v.cpr;
+    }
     v.s_off = (const uint32_t *)P(i_s_off); v.s_len = (const uint32_t *)P(i_s_len);
     v.s_owner = (const uint32_t *)P(i_s_owner); v.s_a = (const uint16_t *)P(i_s_a);
     v.s_wd = (const double *)P(i_s_wd); v.s_wf = (const float *)P(i_s_wf);

@@ -192,6 +192,146 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
     }
 }
 
+// Mixed form: LU of C_occ^T with partial pivoting in FP64 (in shared memory), then the inverse
+// from the factors and G = C C_occ^-1 in FP32, the precision these tables are kept in.
+__global__ void __launch_bounds__(VMC_THREADS)
+k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
+                    uint16_t *occ_list, uint16_t *virt_list, uint32_t *occ_bits, float *G, float *AinvT,
+                    unsigned *status) {
+    const int w = blockIdx.x, sg = blockIdx.y;
+    const int n = sg ? nb : na, nv = M - n;
+    const int ne = na + nb, nw = (M + 31) / 32;
+    const double *C = sg ? Cb : Ca;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double *B = sm;                               // n x ld FP64: LU factors
+    float *LUf = (float *)(B + (size_t)n * ld);   // n x ld FP32 copy of the factors
+    float *Y = LUf + (size_t)n * ld;              // n x ld FP32: inverse being formed
+    __shared__ uint16_t s_occ[VMC_MAX_M], s_virt[VMC_MAX_M];
+    __shared__ uint8_t mark[VMC_MAX_M];
+    __shared__ int perm[VMC_MAX_M];
+    __shared__ int s_piv, s_sing;
+    const uint16_t *occ = occ_list + (size_t)w * ne + (sg ? na : 0);
+    uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
+    for (int k = tid; k < M; k += nt) mark[k] = 0;
+    if (tid == 0) s_sing = 0;
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+        s_occ[c] = occ[c];
+        mark[occ[c]] = 1;
+        perm[c] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int v = 0;
+        for (int k = 0; k < M; ++k)
+            if (!mark[k]) s_virt[v++] = (uint16_t)k;
+    }
+    for (int q = tid; q < nw; q += nt) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int k = q * 32 + b;
+            if (k < M && mark[k]) word |= 1u << b;
+        }
+        occ_bits[((size_t)w * 2 + sg) * nw + q] = word;
+    }
+    for (int t = tid; t < n * n; t += nt) {       // B = C_occ^T: B[x][c] = C[occ[c]][x]
+        const int x = t / n, c = t % n;
+        B[x * ld + c] = C[(size_t)s_occ[c] * n + x];
+    }
+    __syncthreads();
+    for (int s = tid; s < nv; s += nt) vl[s] = s_virt[s];
+    // ---- LU with partial pivoting, FP64: P B = L U (L unit lower, stored below the diagonal)
+    for (int k = 0; k < n; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int idx = k;
+            for (int r = k + lane; r < n; r += 32) {
+                const double v = fabs(B[r * ld + k]);
+                if (v > best) { best = v; idx = r; }
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, m);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+                if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+            }
+            if (lane == 0) {
+                s_piv = idx;
+                if (idx != k) { const int t = perm[k]; perm[k] = perm[idx]; perm[idx] = t; }
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k)
+            for (int c = tid; c < n; c += nt) {
+                const double t = B[k * ld + c];
+                B[k * ld + c] = B[p * ld + c];
+                B[p * ld + c] = t;
+            }
+        __syncthreads();
+        double d = B[k * ld + k];
+        if (d == 0.0) {
+            if (tid == 0) s_sing = 1;
+            d = 1.0;
+        }
+        for (int r = k + 1 + tid; r < n; r += nt) B[r * ld + k] /= d;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int t = tid; t < m * m; t += nt) {
+            const int r = k + 1 + t / m, c = k + 1 + t % m;
+            B[r * ld + c] -= B[r * ld + k] * B[k * ld + c];
+        }
+        __syncthreads();
+    }
+    if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
+    // ---- FP32 inverse from the factors: Y = P (rows), then L^-1, then U^-1
+    for (int t = tid; t < n * n; t += nt) {
+        const int r = t / n, c = t % n;
+        LUf[r * ld + c] = (float)B[r * ld + c];
+    }
+    __syncthreads();
+    for (int t = tid; t < n * n; t += nt) {   // (P B)^-1 = U^-1 L^-1 P: start from the rows of P
+        const int r = t / n, c = t % n;
+        Y[r * ld + c] = perm[r] == c ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {             // forward: L (unit diagonal)
+        const int m = n - k - 1;
+        for (int t = tid; t < m * n; t += nt) {
+            const int r = k + 1 + t / n, c = t % n;
+            Y[r * ld + c] -= LUf[r * ld + k] * Y[k * ld + c];
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {        // backward: U
+        const float dk = LUf[k * ld + k] == 0.0f ? 1.0f : LUf[k * ld + k];
+        for (int c = tid; c < n; c += nt) Y[k * ld + c] /= dk;
+        __syncthreads();
+        for (int t = tid; t < k * n; t += nt) {
+            const int r = t / n, c = t % n;
+            Y[r * ld + c] -= LUf[r * ld + k] * Y[k * ld + c];
+        }
+        __syncthreads();
+    }
+    // Y = B^-1 = (C_occ^T)^-1 = AinvT
+    const size_t gofs = (size_t)w * ((size_t)(M - na) * na + (size_t)(M - nb) * nb) +
+                        (sg ? (size_t)(M - na) * na : 0);
+    const size_t aofs = (size_t)w * ((size_t)na * na + (size_t)nb * nb) + (sg ? (size_t)na * na : 0);
+    for (int t = tid; t < n * n; t += nt) {
+        const int c = t / n, x = t % n;
+        AinvT[aofs + t] = Y[c * ld + x];
+    }
+    for (int t = tid; t < nv * n; t += nt) {
+        const int s = t / n, c = t % n;
+        const double *crow = C + (size_t)s_virt[s] * n;
+        float acc = 0.0f;
+        for (int x = 0; x < n; ++x) acc = fmaf((float)crow[x], Y[c * ld + x], acc);
+        G[gofs + t] = acc;
+    }
+}
+
 // Jastrow sums S_p, and (full init only) Fock sums and the diagonal energy.
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
@@ -325,9 +465,10 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
                 M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
                 (double *)Wk->G, (double *)Wk->AinvT, ctx->d_status);
     } else {
-        e = cudaFuncSetAttribute(k_init_tables<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem_m = sizeof(double) * (size_t)nmax * (nmax + 1) * 2 + 16;
+        e = cudaFuncSetAttribute(k_init_tables_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         if (e == cudaSuccess)
-            k_init_tables<float><<<grid, VMC_THREADS, smem, ctx->stream>>>(
+            k_init_tables_mixed<<<grid, VMC_THREADS, smem_m, ctx->stream>>>(
                 M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
                 (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status);
     }
