@@ -93,6 +93,7 @@ vmc_status vmc_lists_info(const vmc_lists *lists, int64_t *n_singles, int64_t *n
  *   occ_bits  uint32 [W][2][ceil(M/32)]  occupation bit strings per spin (bit k of spatial k)
  *   occ_list  uint16 [W][na+nb]     column c -> occupied spatial orbital (alpha cols, beta cols)
  *   virt_list uint16 [W][(M-na)+(M-nb)]  virtual slot -> unoccupied spatial orbital
+ *   pos       uint16 [W][2M]    spin orbital -> its column if occupied, 0x8000|slot if not
  *   G         real   [W][(M-na)*na + (M-nb)*nb]  virtual rows of G^s = C^s (C^s_occ)^-1,
  *             row = virtual slot, column = occupied column (Eq. R: G_ac = det ratio of i->a)
  *   AinvT     real   [W][na*na + nb*nb]  (C^s_occ)^-1 transposed: AinvT[c][x]
@@ -110,6 +111,7 @@ typedef struct {
     uint32_t *occ_bits;
     uint16_t *occ_list;
     uint16_t *virt_list;
+    uint16_t *pos;
     void *G;
     void *AinvT;
     void *S;
@@ -126,13 +128,13 @@ typedef struct {
 } vmc_params;
 
 /* Element counts of every walker array for W walkers (for allocation by the caller):
-   out[0..9] = occ_bits, occ_list, virt_list, G, AinvT, S, F, e_diag, rng_counter (elements). */
+   out[0..9] = occ_bits, occ_list, virt_list, pos, G, AinvT, S, F, e_diag, rng_counter. */
 vmc_status vmc_walkers_sizes(int W, int M, int n_alpha, int n_beta, const vmc_lists *lists,
-                             int64_t out[9]);
+                             int64_t out[10]);
 
 /*
  * (Re)build every walker table from occ_list (each spin block holds the walker's occupied
- * orbitals in any order) and the parameters: occ_bits, virt_list, C_occ^-1 by FP64 LU with
+ * orbitals in any order) and the parameters: occ_bits, virt_list, pos, C_occ^-1 by FP64 LU with
  * partial pivoting (the one O(N^3) step of Sec. III.B), G = C C_occ^-1, S, F, e_diag.  Also
  * refreshes the Jastrow constants stored with the lists for these parameters.  rng_counter is
  * left as is.  This is the periodic recompute (e.g. every 64 moves, and after every parameter

@@ -65,7 +65,7 @@ static vmc_status check_walkers(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_l
         return set_err(ctx, VMC_ERR_ARG, "electron counts out of range");
     if (Wk->n_alpha + Wk->n_beta < 1) return set_err(ctx, VMC_ERR_ARG, "no electrons");
     if (Wk->precision != VMC_FP64 && Wk->precision != VMC_MIXED) return set_err(ctx, VMC_ERR_ARG, "bad precision");
-    if (!Wk->occ_bits || !Wk->occ_list || !Wk->virt_list || !Wk->G || !Wk->AinvT || !Wk->S || !Wk->F ||
+    if (!Wk->occ_bits || !Wk->occ_list || !Wk->virt_list || !Wk->pos || !Wk->G || !Wk->AinvT || !Wk->S || !Wk->F ||
         !Wk->e_diag || !Wk->rng_counter)
         return set_err(ctx, VMC_ERR_ARG, "null walker array");
     if (L && L->M != Wk->M) return set_err(ctx, VMC_ERR_ARG, "lists and walkers disagree on M");
@@ -126,18 +126,19 @@ vmc_status vmc_sync(vmc_ctx *ctx) {
     return VMC_OK;
 }
 
-vmc_status vmc_walkers_sizes(int W, int M, int na, int nb, const vmc_lists *L, int64_t out[9]) {
+vmc_status vmc_walkers_sizes(int W, int M, int na, int nb, const vmc_lists *L, int64_t out[10]) {
     if (!out || W < 0 || M < 1 || na < 0 || nb < 0 || na > M || nb > M) return VMC_ERR_ARG;
     const int64_t nw = (M + 31) / 32;
     out[0] = (int64_t)W * 2 * nw;
     out[1] = (int64_t)W * (na + nb);
     out[2] = (int64_t)W * (2 * M - na - nb);
-    out[3] = (int64_t)W * (int64_t)walker_stride_G(M, na, nb);
-    out[4] = (int64_t)W * (int64_t)walker_stride_A(na, nb);
-    out[5] = (int64_t)W * 2 * M;
-    out[6] = (int64_t)W * 2 * (L ? L->ns : 0);
-    out[7] = W;
+    out[3] = (int64_t)W * 2 * M;
+    out[4] = (int64_t)W * (int64_t)walker_stride_G(M, na, nb);
+    out[5] = (int64_t)W * (int64_t)walker_stride_A(na, nb);
+    out[6] = (int64_t)W * 2 * M;
+    out[7] = (int64_t)W * 2 * (L ? L->ns : 0);
     out[8] = W;
+    out[9] = W;
     return VMC_OK;
 }
 

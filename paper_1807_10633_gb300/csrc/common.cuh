@@ -43,19 +43,21 @@ struct ListsView {
     int cpr;       // warp chunks (32 candidates) per spin-orbital row
     int n_groups;  // singles blocks of 32 spin orbitals + 2M * cpr row chunks
     int64_t ns, nds, ndo;
-    // singles, CSR over spatial i
+    // singles, CSR over spatial i; records: mixed {a, w_alpha, w_beta, 0} (16 B),
+    // FP64 {a, 0, w_alpha, w_beta} (32 B, the first 8 bytes hold a)
     const uint32_t *s_off, *s_len, *s_owner;
     const uint16_t *s_a;
-    const double *s_wd;      // [2][ns]
-    const float *s_wf;       // [2][ns]
-    // same-spin doubles, CSR over tri(p<q)
+    const float4 *s_rec32;
+    const double4_32a *s_rec64;
+    // same-spin doubles, CSR over tri(p<q); records: mixed {ab, v, w_alpha, w_beta},
+    // FP64 {ab, v, w_alpha, w_beta} with ab in the first 8 bytes
     const uint32_t *ds_off, *ds_len, *ds_ab, *ds_owner;
-    const double *ds_vd, *ds_wd;  // v [nds], w [2][nds]
-    const float *ds_vf, *ds_wf;
-    // opposite-spin doubles, CSR over p*M+q
+    const float4 *ds_rec32;
+    const double4_32a *ds_rec64;
+    // opposite-spin doubles, CSR over p*M+q; records {ab, v, w, 0}
     const uint32_t *do_off, *do_len, *do_ab, *do_owner;
-    const double *do_vd, *do_wd;  // v [ndo], w [ndo]
-    const float *do_vf, *do_wf;
+    const float4 *do_rec32;
+    const double4_32a *do_rec64;
     // Fock-sum update tables: Tj[k][e] = (ai|kk), Tjk[k][e] = (ai|kk) - (ak|ki)
     const double *Tj, *Tjk;
     // diagonal tables: Jd[p][q] = (pp|qq), Kd[p][q] = (pq|qp); hd[p] = h_pp; h1 full

@@ -28,27 +28,35 @@ __device__ __forceinline__ float rexp(float x) { return expf(x); }
 __device__ __forceinline__ double rrcp(double x) { return __ddiv_rn(1.0, x); }
 __device__ __forceinline__ float rrcp(float x) { return __fdiv_rn(1.0f, x); }
 
-template <typename real> __device__ __forceinline__ real lw_single(const ListsView &L, int s, uint32_t e);
-template <> __device__ __forceinline__ double lw_single<double>(const ListsView &L, int s, uint32_t e) { return L.s_wd[(size_t)s * L.ns + e]; }
-template <> __device__ __forceinline__ float lw_single<float>(const ListsView &L, int s, uint32_t e) { return L.s_wf[(size_t)s * L.ns + e]; }
-template <typename real> __device__ __forceinline__ real lw_same(const ListsView &L, int s, uint32_t e);
-template <> __device__ __forceinline__ double lw_same<double>(const ListsView &L, int s, uint32_t e) { return L.ds_wd[(size_t)s * L.nds + e]; }
-template <> __device__ __forceinline__ float lw_same<float>(const ListsView &L, int s, uint32_t e) { return L.ds_wf[(size_t)s * L.nds + e]; }
-template <typename real> __device__ __forceinline__ real lv_same(const ListsView &L, uint32_t e);
-template <> __device__ __forceinline__ double lv_same<double>(const ListsView &L, uint32_t e) { return L.ds_vd[e]; }
-template <> __device__ __forceinline__ float lv_same<float>(const ListsView &L, uint32_t e) { return L.ds_vf[e]; }
-template <typename real> __device__ __forceinline__ real lw_opp(const ListsView &L, uint32_t e);
-template <> __device__ __forceinline__ double lw_opp<double>(const ListsView &L, uint32_t e) { return L.do_wd[e]; }
-template <> __device__ __forceinline__ float lw_opp<float>(const ListsView &L, uint32_t e) { return L.do_wf[e]; }
-template <typename real> __device__ __forceinline__ real lv_opp(const ListsView &L, uint32_t e);
-template <> __device__ __forceinline__ double lv_opp<double>(const ListsView &L, uint32_t e) { return L.do_vd[e]; }
-template <> __device__ __forceinline__ float lv_opp<float>(const ListsView &L, uint32_t e) { return L.do_vf[e]; }
+// One packed list record (16 B in the mixed form, 32 B in the FP64 form): key (a or a|b<<16)
+// and up to three reals.
+template <typename real> struct Rec;
+template <> struct Rec<float> {
+    float4 v;
+    __device__ uint32_t key() const { return __float_as_uint(v.x); }
+    __device__ float f1() const { return v.y; }
+    __device__ float f2() const { return v.z; }
+    __device__ float f3() const { return v.w; }
+};
+template <> struct Rec<double> {
+    double4_32a v;
+    __device__ uint32_t key() const { return (uint32_t)__double_as_longlong(v.x); }
+    __device__ double f1() const { return v.y; }
+    __device__ double f2() const { return v.z; }
+    __device__ double f3() const { return v.w; }
+};
+__device__ __forceinline__ Rec<float> rec_single(const ListsView &L, uint32_t e, float) { return Rec<float>{__ldg(&L.s_rec32[e])}; }
+__device__ __forceinline__ Rec<double> rec_single(const ListsView &L, uint32_t e, double) { return Rec<double>{L.s_rec64[e]}; }
+__device__ __forceinline__ Rec<float> rec_same(const ListsView &L, uint32_t e, float) { return Rec<float>{__ldg(&L.ds_rec32[e])}; }
+__device__ __forceinline__ Rec<double> rec_same(const ListsView &L, uint32_t e, double) { return Rec<double>{L.ds_rec64[e]}; }
+__device__ __forceinline__ Rec<float> rec_opp(const ListsView &L, uint32_t e, float) { return Rec<float>{__ldg(&L.do_rec32[e])}; }
+__device__ __forceinline__ Rec<double> rec_opp(const ListsView &L, uint32_t e, double) { return Rec<double>{L.do_rec64[e]}; }
 
 // Walker arrays (global) and geometry.
 struct WalkerArgs {
     int W, M, na, nb;
     const uint32_t *occ_bits;
-    uint16_t *occ_list, *virt_list;
+    uint16_t *occ_list, *virt_list, *pos;
     uint32_t *occ_bits_w;
     void *G, *AinvT, *S;
     double *F, *e_diag;
@@ -87,7 +95,11 @@ struct Unit {
 template <typename real>
 struct View {
     const uint16_t *pos;   // [2M]: occupied -> column, virtual -> 0x8000 | slot
-    const real *G;         // walker G, shared or global, layout as Geo
+    const real *Ga, *Gb;   // virtual rows of G per spin (shared and padded, or global)
+    int lda, ldb;          // their row strides
+    __device__ const real *Grow(int s, int slot) const {
+        return s ? Gb + (size_t)slot * ldb : Ga + (size_t)slot * lda;
+    }
     const real *E;         // [2M] exp(S) (nullptr: compute from S on the fly)
     const real *S;         // walker S in global (used when E == nullptr)
     const double *F;       // walker F [2][ns]
@@ -174,43 +186,45 @@ __device__ __forceinline__ bool eval_entry(const ListsView &L, const View<real> 
     const int M = V.geo.M;
     if (u.kind == 0) {
         const int s = u.cls;
-        const int a = L.s_a[idx];
+        const Rec<real> r = rec_single(L, idx, real(0));
+        const int a = (int)r.key();
         const uint16_t pa = V.pos[s * M + a];
         if (!(pa & 0x8000)) return false;
-        const int n = V.geo.n(s);
-        const real g = V.G[V.geo.g_off(s) + (size_t)(pa & 0x7FFF) * n + u.ci];
-        const real r = rmul(rmul(rmul(g, lw_single<real>(L, s, idx)), V.Ev(s * M + a)), u.einv);
-        ratio = r;
-        contrib = rmul((real)V.F[(size_t)s * L.ns + idx], r);
+        const real g = V.Grow(s, pa & 0x7FFF)[u.ci];
+        const real w = s ? r.f2() : r.f1();
+        const real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), u.einv);
+        ratio = rt;
+        contrib = rmul((real)V.F[(size_t)s * L.ns + idx], rt);
         A = s * M + a; B = -1;
         return true;
     }
     if (u.kind == 1) {
         const int s = u.cls;
-        const uint32_t ab = L.ds_ab[idx];
+        const Rec<real> r = rec_same(L, idx, real(0));
+        const uint32_t ab = r.key();
         const int a = ab & 0xFFFF, b = ab >> 16;
         const uint16_t pa = V.pos[s * M + a], pb = V.pos[s * M + b];
         if (!(pa & pb & 0x8000)) return false;
-        const int n = V.geo.n(s);
-        const real *Gs = V.G + V.geo.g_off(s);
-        const real *ra = Gs + (size_t)(pa & 0x7FFF) * n, *rb = Gs + (size_t)(pb & 0x7FFF) * n;
+        const real *ra = V.Grow(s, pa & 0x7FFF);
+        const real *rb = V.Grow(s, pb & 0x7FFF);
         const real minor = rsub(rmul(ra[u.ci], rb[u.cj]), rmul(ra[u.cj], rb[u.ci]));
-        const real r = rmul(rmul(rmul(rmul(minor, lw_same<real>(L, s, idx)), V.Ev(s * M + a)),
-                                 V.Ev(s * M + b)), u.einv);
-        ratio = r;
-        contrib = rmul(lv_same<real>(L, idx), r);
+        const real w = s ? r.f3() : r.f2();
+        const real rt = rmul(rmul(rmul(rmul(minor, w), V.Ev(s * M + a)), V.Ev(s * M + b)), u.einv);
+        ratio = rt;
+        contrib = rmul(r.f1(), rt);
         A = s * M + a; B = s * M + b;
         return true;
     }
-    const uint32_t ab = L.do_ab[idx];
+    const Rec<real> r = rec_opp(L, idx, real(0));
+    const uint32_t ab = r.key();
     const int a = ab & 0xFFFF, b = ab >> 16;
     const uint16_t pa = V.pos[a], pb = V.pos[M + b];
     if (!(pa & pb & 0x8000)) return false;
-    const real ga = V.G[(size_t)(pa & 0x7FFF) * V.geo.na + u.ci];
-    const real gb = V.G[V.geo.g_off(1) + (size_t)(pb & 0x7FFF) * V.geo.nb + u.cj];
-    const real r = rmul(rmul(rmul(rmul(rmul(ga, gb), lw_opp<real>(L, idx)), V.Ev(a)), V.Ev(M + b)), u.einv);
-    ratio = r;
-    contrib = rmul(lv_opp<real>(L, idx), r);
+    const real ga = V.Grow(0, pa & 0x7FFF)[u.ci];
+    const real gb = V.Grow(1, pb & 0x7FFF)[u.cj];
+    const real rt = rmul(rmul(rmul(rmul(rmul(ga, gb), r.f2()), V.Ev(a)), V.Ev(M + b)), u.einv);
+    ratio = rt;
+    contrib = rmul(r.f1(), rt);
     A = a; B = M + b;
     return true;
 }
@@ -225,22 +239,6 @@ __device__ __forceinline__ u128 rate_of(real ratio, unsigned *flag) {
     return rate_fixed(r);
 }
 
-// Orbital -> column / virtual-slot map of one walker.
-__device__ void build_pos(const Geo &geo, const uint16_t *occ, const uint16_t *virt, uint16_t *pos) {
-    const int tid = threadIdx.x, nt = blockDim.x, M = geo.M;
-    for (int c = tid; c < geo.ne; c += nt) {
-        const int s = c < geo.na ? 0 : 1;
-        const int col = c - (s ? geo.na : 0);
-        pos[s * M + occ[c]] = (uint16_t)col;
-    }
-    const int nvt = 2 * M - geo.ne;
-    for (int t = tid; t < nvt; t += nt) {
-        const int s = t < geo.nv_a ? 0 : 1;
-        const int slot = t - (s ? geo.nv_a : 0);
-        pos[s * M + virt[t]] = (uint16_t)(0x8000 | slot);
-    }
-}
-
 template <typename real> struct AccT { typedef double type; };
 template <> struct AccT<float> { typedef float type; };
 
@@ -250,41 +248,49 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
                u128 *__restrict__ rates, unsigned *status) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    const int M = geo.M, ne = geo.ne, n_groups = L.n_groups;
+    const int M = geo.M, n_groups = L.n_groups;
+    const int lda = geo.na + 1, ldb = geo.nb + 1;    // padded rows: no bank conflicts on columns
     extern __shared__ __align__(16) unsigned char smraw[];
-    real *sG = (real *)smraw;
-    real *sE = sG + geo.g_stride;
-    uint16_t *pos = (uint16_t *)(sE + 2 * M);
-    __shared__ double red_e[VMC_WARPS];
+    real *sGa = (real *)smraw;
+    real *sGb = sGa + (size_t)geo.nv_a * lda;
+    real *sE = sGb + (size_t)geo.nv_b * ldb;
+    double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
+    uint16_t *pos = (uint16_t *)(eg + n_groups);
     __shared__ u128 red_q[VMC_WARPS];
+    __shared__ int next_group;
 
-    // ---- prologue: stage G (vectorised), exp(S), orbital map
+    // ---- prologue: stage G into padded rows, exp(S), orbital map
     {
         const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
-        const size_t nbytes = geo.g_stride * sizeof(real);
-        const int4 *src = (const int4 *)Gw;
-        int4 *dst = (int4 *)sG;
-        const size_t n16 = nbytes / 16;
-        if ((((uintptr_t)Gw) & 15) == 0) {
-            for (size_t t = tid; t < n16; t += nt) dst[t] = src[t];
-            for (size_t t = n16 * 16 / sizeof(real) + tid; t < geo.g_stride; t += nt) sG[t] = Gw[t];
-        } else {
-            for (size_t t = tid; t < geo.g_stride; t += nt) sG[t] = Gw[t];
+        const size_t na_el = (size_t)geo.nv_a * geo.na;
+        for (size_t t = tid; t < geo.g_stride; t += nt) {
+            const real v = Gw[t];
+            if (t < na_el) {
+                const size_t r = t / geo.na, c = t - r * geo.na;
+                sGa[r * lda + c] = v;
+            } else {
+                const size_t u = t - na_el, r = u / geo.nb, c = u - r * geo.nb;
+                sGb[r * ldb + c] = v;
+            }
         }
         const real *Sw = (const real *)A.S + (size_t)w * 2 * M;
         for (int p = tid; p < 2 * M; p += nt) sE[p] = rexp(Sw[p]);
-        build_pos(geo, A.occ_list + (size_t)w * ne, A.virt_list + (size_t)w * (2 * M - ne), pos);
+        const uint16_t *pw = A.pos + (size_t)w * 2 * M;
+        for (int p = tid; p < 2 * M; p += nt) pos[p] = pw[p];
+        if (tid == 0) next_group = VMC_WARPS;
     }
     __syncthreads();
 
     View<real> V;
-    V.pos = pos; V.G = sG; V.E = sE; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+    V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
+    V.E = sE; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
     typedef typename AccT<real>::type acc_t;
-    double e_acc = 0.0;
     u128 q_tot = 0;
     unsigned flag = 0;
 
-    for (int g = warp; g < n_groups; g += VMC_WARPS) {
+    // groups are taken dynamically; each group's sums are stored by index, so the result does not
+    // depend on which warp took it
+    for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -303,26 +309,36 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
                 }
             }
         }
-        e_acc += (double)e_grp;
+        const double eg_sum = warp_sum_f64((double)e_grp);
         q_grp = warp_sum_u128(q_grp);
-        if (lane == 0) rates[(size_t)w * n_groups + g] = q_grp;
+        if (lane == 0) {
+            rates[(size_t)w * n_groups + g] = q_grp;
+            eg[g] = eg_sum;
+        }
         q_tot += q_grp;
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&next_group, 1);
+        g = __shfl_sync(0xffffffffu, nxt, 0);
     }
-    e_acc = warp_sum_f64(e_acc);
-    if (lane == 0) { red_e[warp] = e_acc; red_q[warp] = q_tot; }
+    if (lane == 0) red_q[warp] = q_tot;
     if (flag) atomicOr(status, flag);
     __syncthreads();
-    if (tid == 0) {
-        double s = A.e_diag[w];
-        u128 Q = 0;
-        for (int k = 0; k < VMC_WARPS; ++k) { s += red_e[k]; Q += red_q[k]; }
-        e_loc[w] = s;
-        if (Q == 0) {
-            t_res[w] = 0.0;
-            atomicOr(status, VMC_DEV_NOMOVE);
-        } else {
-            const double qh = (double)(uint64_t)(Q >> 64), ql = (double)(uint64_t)Q;
-            t_res[w] = __ddiv_rn(1.0, __dadd_rn(qh, __dmul_rn(ql, 0x1p-64)));
+    if (warp == 0) {
+        // fixed-order sum of the per-group energies: lane l takes groups l, l+32, ...
+        double s = 0.0;
+        for (int g = lane; g < n_groups; g += 32) s += eg[g];
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            u128 Q = 0;
+            for (int k = 0; k < VMC_WARPS; ++k) Q += red_q[k];
+            e_loc[w] = A.e_diag[w] + s;
+            if (Q == 0) {
+                t_res[w] = 0.0;
+                atomicOr(status, VMC_DEV_NOMOVE);
+            } else {
+                const double qh = (double)(uint64_t)(Q >> 64), ql = (double)(uint64_t)Q;
+                t_res[w] = __ddiv_rn(1.0, __dadd_rn(qh, __dmul_rn(ql, 0x1p-64)));
+            }
         }
     }
 }
@@ -348,7 +364,8 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
     uint16_t *occ = A.occ_list + (size_t)w * ne;
     uint16_t *virt = A.virt_list + (size_t)w * (2 * M - ne);
     uint32_t *bits = A.occ_bits_w + (size_t)w * 2 * geo.nw;
-    build_pos(geo, occ, virt, pos);
+    uint16_t *posw = A.pos + (size_t)w * N2;
+    for (int p = tid; p < N2; p += nt) pos[p] = posw[p];
     __syncthreads();
 
     // ---- choose the group (warp 0), then the entry inside it
@@ -383,7 +400,8 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
         if (gsel >= 0) {
             const u128 Tl = T - before;   // threshold inside the group
             View<real> V;
-            V.pos = pos; V.G = Gw; V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+            V.pos = pos; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
+            V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
             Unit<real> u;
             const bool act = setup_unit<real>(L, V, gsel, lane, u);
             unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -546,7 +564,14 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
         if (tid == 0) {
             occs[ci] = (uint16_t)to[st][0];
             virts[sa] = (uint16_t)fr[st][0];
-            if (rk[st] == 2) { occs[cj] = (uint16_t)to[st][1]; virts[sb] = (uint16_t)fr[st][1]; }
+            posw[s * M + to[st][0]] = (uint16_t)ci;
+            posw[s * M + fr[st][0]] = (uint16_t)(0x8000 | sa);
+            if (rk[st] == 2) {
+                occs[cj] = (uint16_t)to[st][1];
+                virts[sb] = (uint16_t)fr[st][1];
+                posw[s * M + to[st][1]] = (uint16_t)cj;
+                posw[s * M + fr[st][1]] = (uint16_t)(0x8000 | sb);
+            }
             uint32_t *bw = bits + s * geo.nw;
             for (int k = 0; k < rk[st]; ++k) {
                 const int f = fr[st][k], tt = to[st][k];
@@ -564,7 +589,7 @@ static WalkerArgs make_args(vmc_walkers *Wk) {
     WalkerArgs A;
     A.W = Wk->W; A.M = Wk->M; A.na = Wk->n_alpha; A.nb = Wk->n_beta;
     A.occ_bits = Wk->occ_bits; A.occ_bits_w = Wk->occ_bits;
-    A.occ_list = Wk->occ_list; A.virt_list = Wk->virt_list;
+    A.occ_list = Wk->occ_list; A.virt_list = Wk->virt_list; A.pos = Wk->pos;
     A.G = Wk->G; A.AinvT = Wk->AinvT; A.S = Wk->S; A.F = Wk->F; A.e_diag = Wk->e_diag;
     A.rng = Wk->rng_counter;
     return A;
@@ -575,8 +600,9 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const int M = Wk->M;
     (void)n_groups;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
-    const size_t gst = walker_stride_G(M, Wk->n_alpha, Wk->n_beta);
-    const size_t smem = esz * (gst + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16;
+    const int na = Wk->n_alpha, nb = Wk->n_beta;
+    const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
+    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e;

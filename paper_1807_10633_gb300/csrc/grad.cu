@@ -1,8 +1,9 @@
 // Gradient ratios (Sec. III.B) summed over walkers with per-walker weights (a vector-Jacobian
 // product of ln psi), AMSGrad (Sec. II.C, Eqs. m1-m2) and the walker sums of Eq. (vmc).
 //
-// The walker sums are deterministic: each CTA reduces a fixed chunk of walkers into a partial
-// buffer and a second kernel adds the partials in chunk order.
+// The walker sums are deterministic: the Jastrow block is an exact 64-bit fixed-point sum, and
+// for the orbital block each CTA reduces a fixed chunk of walkers into a partial buffer that a
+// second kernel adds in chunk order.
 #include <math.h>
 
 #include "common.cuh"
@@ -11,6 +12,7 @@ namespace {
 
 constexpr int kChunkJ = 1024;   // walkers per CTA for dJ
 constexpr int kChunkC = 256;    // walkers per CTA for dC
+constexpr int kRowsC = 16;      // orbital rows per CTA (registers per thread) for dC
 
 // 32 consecutive spin-orbital occupation bits starting at spin orbital p0 (lane l -> bit l)
 __device__ __forceinline__ uint32_t window_bits(const uint32_t *bits_w, int M, int nw, int p0, int lane) {
@@ -29,34 +31,69 @@ __device__ __forceinline__ void weights(int mode, const double *t, const double 
     c1 = mode ? c0 * e[w] : 0.0;
 }
 
+// Fixed-point weights for the Jastrow gradient: cq = round(c 2^s) with s chosen from sum |c| so that
+// no partial sum can overflow 63 bits; integer sums are then exact and order independent.
+// Also adds sum c0 and sum c1 to sums[0..1] (mode 1).  One CTA.
+__global__ void __launch_bounds__(1024)
+k_weight_prep(int W, const double *__restrict__ t, const double *__restrict__ e, int mode,
+              long long *__restrict__ cq, int *__restrict__ sexp, double *__restrict__ sums) {
+    __shared__ double r[4][32];
+    __shared__ int s_exp[2];
+    double a0 = 0.0, a1 = 0.0, s0 = 0.0, s1 = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double c0, c1;
+        weights(mode, t, e, w, c0, c1);
+        a0 += fabs(c0); a1 += fabs(c1); s0 += c0; s1 += c1;
+    }
+    a0 = warp_sum_f64(a0); a1 = warp_sum_f64(a1); s0 = warp_sum_f64(s0); s1 = warp_sum_f64(s1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { r[0][warp] = a0; r[1][warp] = a1; r[2][warp] = s0; r[3][warp] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A0 = 0.0, A1 = 0.0, S0 = 0.0, S1 = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { A0 += r[0][k]; A1 += r[1][k]; S0 += r[2][k]; S1 += r[3][k]; }
+        s_exp[0] = A0 > 0.0 ? 61 - ilogb(A0) : 0;
+        s_exp[1] = A1 > 0.0 ? 61 - ilogb(A1) : 0;
+        sexp[0] = s_exp[0];
+        sexp[1] = s_exp[1];
+        if (sums) { sums[0] += S0; sums[1] += S1; }
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double c0, c1;
+        weights(mode, t, e, w, c0, c1);
+        cq[w] = __double2ll_rn(scalbn(c0, s_exp[0]));
+        if (mode) cq[W + w] = __double2ll_rn(scalbn(c1, s_exp[1]));
+    }
+}
+
 // dJ partials: tile (P, Q) of 32 x 32 spin orbitals with P <= Q, walker chunk blockIdx.y.
-// part layout: [n_out][chunk][N2][N2].
+// Exact 64-bit integer sums of the fixed-point weights.  part layout: [n_out][chunk][N2][N2].
 __global__ void __launch_bounds__(256)
-k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const double *__restrict__ wgt,
-         const double *__restrict__ e, int mode, double *__restrict__ part) {
+k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const long long *__restrict__ cq, int mode,
+         long long *__restrict__ part) {
     const int N2 = 2 * M, nw = (M + 31) / 32, T = (N2 + 31) / 32;
     int t = blockIdx.x, P = 0;
     while (t >= T - P) { t -= T - P; ++P; }
     const int Q = P + t;
     const int tid = threadIdx.x, lane = tid & 31;
     const int pl = tid >> 3, ql0 = (tid & 7) * 4;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0}, acc2[4] = {0.0, 0.0, 0.0, 0.0};
+    long long acc[4] = {0, 0, 0, 0}, acc2[4] = {0, 0, 0, 0};
     const int w0 = blockIdx.y * kChunkJ, w1 = min(W, w0 + kChunkJ);
     for (int w = w0; w < w1; ++w) {
         const uint32_t *bw = bits + (size_t)w * 2 * nw;
         const uint32_t bp = window_bits(bw, M, nw, P * 32, lane);
         const uint32_t bq = window_bits(bw, M, nw, Q * 32, lane);
         if ((bp >> pl) & 1u) {
-            double c0, c1;
-            weights(mode, wgt, e, w, c0, c1);
+            const long long c0 = cq[w], c1 = mode ? cq[W + w] : 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if ((bq >> (ql0 + k)) & 1u) { acc[k] += c0; acc2[k] += c1; }
         }
     }
     const size_t chunk_sz = (size_t)N2 * N2;
-    double *dst = part + (size_t)blockIdx.y * chunk_sz;
-    double *dst2 = part + ((size_t)gridDim.y + blockIdx.y) * chunk_sz;
+    long long *dst = part + (size_t)blockIdx.y * chunk_sz;
+    long long *dst2 = part + ((size_t)gridDim.y + blockIdx.y) * chunk_sz;
     const int p = P * 32 + pl;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -68,59 +105,69 @@ k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const double *__restri
     }
 }
 
-__global__ void k_reduce_J(int M, int n_chunks, const double *__restrict__ part, double *__restrict__ dJ,
-                           double *__restrict__ dJ2) {
+__global__ void k_reduce_J(int M, int n_chunks, const long long *__restrict__ part, const int *__restrict__ sexp,
+                           double *__restrict__ dJ, double *__restrict__ dJ2) {
     const int N2 = 2 * M;
     const size_t csz = (size_t)N2 * N2;
+    const int e0 = sexp[0], e1 = sexp[1];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N2 * N2; t += gridDim.x * blockDim.x) {
         const int p = t / N2, q = t % N2;
         if (p > q) continue;
-        double s = 0.0, s2 = 0.0;
+        long long s = 0, s2 = 0;
         for (int c = 0; c < n_chunks; ++c) s += part[(size_t)c * csz + t];
-        dJ[t] += s;
+        dJ[t] += scalbn((double)s, -e0);
         if (dJ2) {
             for (int c = 0; c < n_chunks; ++c) s2 += part[((size_t)n_chunks + c) * csz + t];
-            dJ2[t] += s2;
+            dJ2[t] += scalbn((double)s2, -e1);
         }
     }
 }
 
-// dC partials for spin blockIdx.x, walker chunk blockIdx.y: acc[k][x] += w AinvT[col(k)][x]
-// part layout: [n_out][chunk][2][M][nmax]
-template <typename real>
-__global__ void __launch_bounds__(256)
-k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ occ_list, const real *__restrict__ AinvT,
+// dC partials: CTA = (spin, block of kRowsC orbital rows) x walker chunk; thread x owns the
+// accumulators dC[k][x] of its rows in registers: acc[k][x] += c_w AinvT_w[pos_w(k)][x] for
+// occupied k.  part layout: [n_out][chunk][2][M][nmax].  acc_t = float (mixed) or double.
+template <typename real, typename acc_t>
+__global__ void __launch_bounds__(128)
+k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ pos, const real *__restrict__ AinvT,
          const double *__restrict__ wgt, const double *__restrict__ e, int mode, double *__restrict__ part) {
-    const int s = blockIdx.x, n = s ? nb : na, ne = na + nb;
-    extern __shared__ double acc[];   // [M][n], then (mode 1) a second [M][n]
-    double *acc2 = acc + (size_t)M * n;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < (mode + 1) * M * n; t += nt) acc[t] = 0.0;
-    __syncthreads();
+    const int nrb = (M + kRowsC - 1) / kRowsC;
+    const int s = blockIdx.x / nrb, rb = blockIdx.x - s * nrb;
+    const int n = s ? nb : na, x = threadIdx.x;
+    const int k0 = rb * kRowsC;
+    acc_t acc[kRowsC], acc2[kRowsC];
+#pragma unroll
+    for (int r = 0; r < kRowsC; ++r) { acc[r] = 0; acc2[r] = 0; }
     const size_t astride = (size_t)na * na + (size_t)nb * nb;
     const size_t aoff = s ? (size_t)na * na : 0;
     const int w0 = blockIdx.y * kChunkC, w1 = min(W, w0 + kChunkC);
+    const bool xin = x < n;
     for (int w = w0; w < w1; ++w) {
-        double c0, c1;
-        weights(mode, wgt, e, w, c0, c1);
-        const uint16_t *occ = occ_list + (size_t)w * ne + (s ? na : 0);
+        double c0d, c1d;
+        weights(mode, wgt, e, w, c0d, c1d);
+        const acc_t c0 = (acc_t)c0d, c1 = (acc_t)c1d;
+        const uint16_t *pw = pos + (size_t)w * 2 * M + (size_t)s * M + k0;
         const real *A = AinvT + (size_t)w * astride + aoff;
-        for (int t = tid; t < n * n; t += nt) {
-            const int col = t / n, x = t - col * n;
-            const double a = (double)A[t];
-            const size_t o = (size_t)occ[col] * n + x;
-            acc[o] += c0 * a;
-            if (mode) acc2[o] += c1 * a;
+#pragma unroll
+        for (int r = 0; r < kRowsC; ++r) {
+            if (k0 + r >= M) break;
+            const uint16_t pc = pw[r];
+            if (!(pc & 0x8000) && xin) {
+                const acc_t a = (acc_t)A[(size_t)pc * n + x];
+                acc[r] += c0 * a;
+                if (mode) acc2[r] += c1 * a;
+            }
         }
-        __syncthreads();   // the next walker maps columns to different rows
     }
-    __syncthreads();
+    if (!xin) return;
     const size_t blk = (size_t)M * (na > nb ? na : nb);
     double *dst = part + ((size_t)blockIdx.y * 2 + s) * blk;
-    for (int t = tid; t < M * n; t += nt) dst[t] = acc[t];
-    if (mode) {
-        double *dst2 = part + (((size_t)gridDim.y + blockIdx.y) * 2 + s) * blk;
-        for (int t = tid; t < M * n; t += nt) dst2[t] = acc2[t];
+    double *dst2 = part + (((size_t)gridDim.y + blockIdx.y) * 2 + s) * blk;
+#pragma unroll
+    for (int r = 0; r < kRowsC; ++r) {
+        const int k = k0 + r;
+        if (k >= M) break;
+        dst[(size_t)k * n + x] = (double)acc[r];
+        if (mode) dst2[(size_t)k * n + x] = (double)acc2[r];
     }
 }
 
@@ -184,45 +231,45 @@ k_walker_reduce(int W, const double *__restrict__ t, const double *__restrict__ 
 }  // namespace
 
 static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e, int mode,
-                            double *const out0[3], double *const out1[3]) {
+                            double *const out0[3], double *const out1[3], double *sums) {
     const int W = Wk->W, M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta, N2 = 2 * M;
     const int T = (N2 + 31) / 32, ntile = T * (T + 1) / 2;
     const int cj = (W + kChunkJ - 1) / kChunkJ, cc = (W + kChunkC - 1) / kChunkC;
     const int nmax = na > nb ? na : nb, nout = mode + 1;
-    const size_t bytes_J = sizeof(double) * (size_t)nout * cj * N2 * N2;
+    if (nmax > 128) return set_err(ctx, VMC_ERR_ARG, "n_sigma > 128 is not supported by the gradient kernel");
+    const size_t head = 256 + sizeof(long long) * 2 * (size_t)W;
+    const size_t bytes_J = sizeof(long long) * (size_t)nout * cj * N2 * N2;
     const size_t bytes_C = sizeof(double) * (size_t)nout * cc * 2 * M * nmax;
-    vmc_status st = ensure_workspace(ctx, bytes_J > bytes_C ? bytes_J : bytes_C);
+    vmc_status st = ensure_workspace(ctx, head + (bytes_J > bytes_C ? bytes_J : bytes_C));
     if (st) return st;
-    double *part = (double *)ctx->ws;
+    int *sexp = (int *)ctx->ws;
+    long long *cq = (long long *)((char *)ctx->ws + 256);
+    void *part = (char *)ctx->ws + head;
+    k_weight_prep<<<1, 1024, 0, ctx->stream>>>(W, t, e, mode, cq, sexp, sums);
+    ctx->launches += 1;
     if (out0[0]) {
-        k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, t, e, mode, part);
-        k_reduce_J<<<(N2 * N2 + 255) / 256, 256, 0, ctx->stream>>>(M, cj, part, out0[0], mode ? out1[0] : nullptr);
+        k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, cq, mode, (long long *)part);
+        k_reduce_J<<<(N2 * N2 + 255) / 256, 256, 0, ctx->stream>>>(M, cj, (const long long *)part, sexp, out0[0],
+                                                                   mode ? out1[0] : nullptr);
         ctx->launches += 2;
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return cuda_check(ctx, err, "k_grad_J");
     }
     if (out0[1] && out0[2]) {
-        const size_t smem = sizeof(double) * (size_t)nout * M * nmax;
-        if (smem > 227 * 1024) return set_err(ctx, VMC_ERR_ARG, "M * n_sigma too large for the gradient kernel");
-        cudaError_t err;
-        if (Wk->precision == VMC_FP64) {
-            err = cudaFuncSetAttribute(k_grad_C<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err == cudaSuccess)
-                k_grad_C<double><<<dim3(2, cc), 256, smem, ctx->stream>>>(W, M, na, nb, Wk->occ_list,
-                                                                          (const double *)Wk->AinvT, t, e, mode, part);
-        } else {
-            err = cudaFuncSetAttribute(k_grad_C<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err == cudaSuccess)
-                k_grad_C<float><<<dim3(2, cc), 256, smem, ctx->stream>>>(W, M, na, nb, Wk->occ_list,
-                                                                         (const float *)Wk->AinvT, t, e, mode, part);
-        }
-        if (err == cudaSuccess) {
-            const int tot = nout * (M * na + M * nb);
-            k_reduce_C<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, cc, nout, part, out0[1], out0[2],
-                                                                   mode ? out1[1] : nullptr, mode ? out1[2] : nullptr);
-        }
+        const int nrb = (M + kRowsC - 1) / kRowsC;
+        const int threads = ((nmax + 31) / 32) * 32;
+        dim3 grid(2 * nrb, cc);
+        if (Wk->precision == VMC_FP64)
+            k_grad_C<double, double><<<grid, threads, 0, ctx->stream>>>(W, M, na, nb, Wk->pos, (const double *)Wk->AinvT,
+                                                                        t, e, mode, (double *)part);
+        else
+            k_grad_C<float, float><<<grid, threads, 0, ctx->stream>>>(W, M, na, nb, Wk->pos, (const float *)Wk->AinvT,
+                                                                      t, e, mode, (double *)part);
+        const int tot = nout * (M * na + M * nb);
+        k_reduce_C<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, cc, nout, (const double *)part, out0[1],
+                                                               out0[2], mode ? out1[1] : nullptr, mode ? out1[2] : nullptr);
         ctx->launches += 2;
-        if (err == cudaSuccess) err = cudaGetLastError();
+        cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return cuda_check(ctx, err, "k_grad_C");
     }
     return VMC_OK;
@@ -232,14 +279,12 @@ vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, dou
                        double *dCb) {
     double *const o0[3] = {dJ, dCa, dCb};
     double *const o1[3] = {nullptr, nullptr, nullptr};
-    return grad_impl(ctx, Wk, w, nullptr, 0, o0, o1);
+    return grad_impl(ctx, Wk, w, nullptr, 0, o0, o1, nullptr);
 }
 
 vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,
                              double *const aO[3], double *const aEO[3], double *sums) {
-    vmc_status st = grad_impl(ctx, Wk, t, e, 1, aO, aEO);
-    if (st) return st;
-    return launch_walker_reduce(ctx, Wk->W, t, e, sums);
+    return grad_impl(ctx, Wk, t, e, 1, aO, aEO, sums);
 }
 
 vmc_status launch_amsgrad(vmc_ctx *ctx, double *p, const double *g, double *m, double *n, size_t np,

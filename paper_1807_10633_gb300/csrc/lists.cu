@@ -146,7 +146,6 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     std::vector<uint16_t> s_a(ns + 1);
     std::vector<uint32_t> s_owner(ns + 1), ds_ab(nds + 1), ds_owner(nds + 1), do_ab(ndo + 1), do_owner(ndo + 1);
     std::vector<double> ds_vd(nds + 1), do_vd(ndo + 1);
-    std::vector<float> ds_vf(nds + 1), do_vf(ndo + 1);
     for (int i = 0; i < M; ++i)
         for (size_t k = 0; k < sl[i].size(); ++k) {
             const size_t e = L->h_s_off[i] + k;
@@ -163,7 +162,6 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
             ds_ab[e] = (uint32_t)dl[t][k].a | ((uint32_t)dl[t][k].b << 16);
             ds_owner[e] = (uint32_t)p | ((uint32_t)q << 16);
             ds_vd[e] = dl[t][k].v;
-            ds_vf[e] = (float)dl[t][k].v;
             L->h_ds_key[e] = dl[t][k].key;
         }
     }
@@ -173,9 +171,25 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
             do_ab[e] = (uint32_t)ol[t][k].a | ((uint32_t)ol[t][k].b << 16);
             do_owner[e] = (uint32_t)(t / M) | ((uint32_t)(t % M) << 16);
             do_vd[e] = ol[t][k].v;
-            do_vf[e] = (float)ol[t][k].v;
             L->h_do_key[e] = ol[t][k].key;
         }
+    // packed per-entry records (the Jastrow constants are rewritten by every refresh)
+    std::vector<float4> s_r32(ns + 1), ds_r32(nds + 1), do_r32(ndo + 1);
+    std::vector<double4_32a> s_r64(ns + 1), ds_r64(nds + 1), do_r64(ndo + 1);
+    auto bits_d = [](uint32_t u) { double d = 0.0; uint64_t x = u; memcpy(&d, &x, 8); return d; };
+    auto bits_f = [](uint32_t u) { float f; memcpy(&f, &u, 4); return f; };
+    for (int64_t e = 0; e < ns; ++e) {
+        s_r32[e] = make_float4(bits_f(s_a[e]), 1.0f, 1.0f, 0.0f);
+        s_r64[e] = make_double4_32a(bits_d(s_a[e]), 0.0, 1.0, 1.0);
+    }
+    for (int64_t e = 0; e < nds; ++e) {
+        ds_r32[e] = make_float4(bits_f(ds_ab[e]), (float)ds_vd[e], 1.0f, 1.0f);
+        ds_r64[e] = make_double4_32a(bits_d(ds_ab[e]), ds_vd[e], 1.0, 1.0);
+    }
+    for (int64_t e = 0; e < ndo; ++e) {
+        do_r32[e] = make_float4(bits_f(do_ab[e]), (float)do_vd[e], 1.0f, 0.0f);
+        do_r64[e] = make_double4_32a(bits_d(do_ab[e]), do_vd[e], 1.0, 0.0);
+    }
     // Fock tables and diagonal tables
     std::vector<double> Tj(MM * (ns + 1)), Tjk(MM * (ns + 1)), Jd(MM * MM), Kd(MM * MM), hd(MM);
     for (int64_t e = 0; e < ns; ++e) {
@@ -207,24 +221,20 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     const size_t i_s_len = add(nullptr, sizeof(uint32_t) * M);
     const size_t i_s_owner = add(s_owner.data(), sizeof(uint32_t) * ns);
     const size_t i_s_a = add(s_a.data(), sizeof(uint16_t) * ns);
-    const size_t i_s_wd = add(nullptr, sizeof(double) * 2 * ns);
-    const size_t i_s_wf = add(nullptr, sizeof(float) * 2 * ns);
+    const size_t i_s_r32 = add(s_r32.data(), sizeof(float4) * ns);
+    const size_t i_s_r64 = add(s_r64.data(), sizeof(double4_32a) * ns);
     const size_t i_ds_off = add(L->h_ds_off, sizeof(uint32_t) * (npair + 1));
     const size_t i_ds_len = add(nullptr, sizeof(uint32_t) * (npair > 0 ? npair : 1));
     const size_t i_ds_ab = add(ds_ab.data(), sizeof(uint32_t) * nds);
     const size_t i_ds_owner = add(ds_owner.data(), sizeof(uint32_t) * nds);
-    const size_t i_ds_vd = add(ds_vd.data(), sizeof(double) * nds);
-    const size_t i_ds_vf = add(ds_vf.data(), sizeof(float) * nds);
-    const size_t i_ds_wd = add(nullptr, sizeof(double) * 2 * nds);
-    const size_t i_ds_wf = add(nullptr, sizeof(float) * 2 * nds);
+    const size_t i_ds_r32 = add(ds_r32.data(), sizeof(float4) * nds);
+    const size_t i_ds_r64 = add(ds_r64.data(), sizeof(double4_32a) * nds);
     const size_t i_do_off = add(L->h_do_off, sizeof(uint32_t) * (MM * MM + 1));
     const size_t i_do_len = add(nullptr, sizeof(uint32_t) * MM * MM);
     const size_t i_do_ab = add(do_ab.data(), sizeof(uint32_t) * ndo);
     const size_t i_do_owner = add(do_owner.data(), sizeof(uint32_t) * ndo);
-    const size_t i_do_vd = add(do_vd.data(), sizeof(double) * ndo);
-    const size_t i_do_vf = add(do_vf.data(), sizeof(float) * ndo);
-    const size_t i_do_wd = add(nullptr, sizeof(double) * ndo);
-    const size_t i_do_wf = add(nullptr, sizeof(float) * ndo);
+    const size_t i_do_r32 = add(do_r32.data(), sizeof(float4) * ndo);
+    const size_t i_do_r64 = add(do_r64.data(), sizeof(double4_32a) * ndo);
     const size_t i_Tj = add(Tj.data(), sizeof(double) * MM * ns);
     const size_t i_Tjk = add(Tjk.data(), sizeof(double) * MM * ns);
     const size_t i_Jd = add(Jd.data(), sizeof(double) * MM * MM);
@@ -270,15 +280,13 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     }
     v.s_off = (const uint32_t *)P(i_s_off); v.s_len = (const uint32_t *)P(i_s_len);
     v.s_owner = (const uint32_t *)P(i_s_owner); v.s_a = (const uint16_t *)P(i_s_a);
-    v.s_wd = (const double *)P(i_s_wd); v.s_wf = (const float *)P(i_s_wf);
+    v.s_rec32 = (const float4 *)P(i_s_r32); v.s_rec64 = (const double4_32a *)P(i_s_r64);
     v.ds_off = (const uint32_t *)P(i_ds_off); v.ds_len = (const uint32_t *)P(i_ds_len);
     v.ds_ab = (const uint32_t *)P(i_ds_ab); v.ds_owner = (const uint32_t *)P(i_ds_owner);
-    v.ds_vd = (const double *)P(i_ds_vd); v.ds_vf = (const float *)P(i_ds_vf);
-    v.ds_wd = (const double *)P(i_ds_wd); v.ds_wf = (const float *)P(i_ds_wf);
+    v.ds_rec32 = (const float4 *)P(i_ds_r32); v.ds_rec64 = (const double4_32a *)P(i_ds_r64);
     v.do_off = (const uint32_t *)P(i_do_off); v.do_len = (const uint32_t *)P(i_do_len);
     v.do_ab = (const uint32_t *)P(i_do_ab); v.do_owner = (const uint32_t *)P(i_do_owner);
-    v.do_vd = (const double *)P(i_do_vd); v.do_vf = (const float *)P(i_do_vf);
-    v.do_wd = (const double *)P(i_do_wd); v.do_wf = (const float *)P(i_do_wf);
+    v.do_rec32 = (const float4 *)P(i_do_r32); v.do_rec64 = (const double4_32a *)P(i_do_r64);
     v.Tj = (const double *)P(i_Tj); v.Tjk = (const double *)P(i_Tjk);
     v.Jd = (const double *)P(i_Jd); v.Kd = (const double *)P(i_Kd);
     v.hd = (const double *)P(i_hd); v.h1 = (const double *)P(i_h1);
@@ -324,8 +332,8 @@ __global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J) {
             const int I = sg * M + (int)L.s_owner[e], A = sg * M + L.s_a[e];
             lw = -jget(J, N2, A, I) + jget(J, N2, A, A) - jget(J, N2, I, I);
             const double w = exp(lw);
-            ((double *)L.s_wd)[sg * L.ns + e] = w;
-            ((float *)L.s_wf)[sg * L.ns + e] = (float)w;
+            ((double *)&L.s_rec64[e])[2 + sg] = w;
+            ((float *)&L.s_rec32[e])[1 + sg] = (float)w;
             continue;
         }
         int I, Jj, A, B;
@@ -350,11 +358,11 @@ __global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J) {
              + jget(J, N2, A, A) + jget(J, N2, B, B) - jget(J, N2, I, I) - jget(J, N2, Jj, Jj);
         const double w = exp(lw);
         if (cls < 2) {
-            ((double *)L.ds_wd)[cls * L.nds + e] = w;
-            ((float *)L.ds_wf)[cls * L.nds + e] = (float)w;
+            ((double *)&L.ds_rec64[e])[2 + cls] = w;
+            ((float *)&L.ds_rec32[e])[2 + cls] = (float)w;
         } else {
-            ((double *)L.do_wd)[e] = w;
-            ((float *)L.do_wf)[e] = (float)w;
+            ((double *)&L.do_rec64[e])[2] = w;
+            ((float *)&L.do_rec32[e])[2] = (float)w;
         }
     }
 }

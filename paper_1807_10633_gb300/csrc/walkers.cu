@@ -127,8 +127,8 @@ __device__ void lu_logdet(double *B, int n, int ld, int *s_piv, double *s_acc, d
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
-              uint16_t *occ_list, uint16_t *virt_list, uint32_t *occ_bits, real *G, real *AinvT,
-              unsigned *status) {
+              uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, real *G,
+              real *AinvT, unsigned *status) {
     const int w = blockIdx.x, sg = blockIdx.y;
     const int n = sg ? nb : na, nv = M - n;
     const int ne = na + nb, nw = (M + 31) / 32;
@@ -171,7 +171,14 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
         B[x * ld + c] = C[(size_t)s_occ[c] * n + x];
     }
     __syncthreads();
-    for (int s = tid; s < nv; s += nt) vl[s] = s_virt[s];
+    {
+        uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)sg * M;
+        for (int s = tid; s < nv; s += nt) {
+            vl[s] = s_virt[s];
+            pw[s_virt[s]] = (uint16_t)(0x8000 | s);
+        }
+        for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
+    }
     if (n > 0) gj_invert(B, X, n, ld, colk, &s_piv, &s_sing);   // X = (C_occ^T)^-1 = AinvT
     __syncthreads();
     if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
@@ -196,8 +203,8 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
 // from the factors and G = C C_occ^-1 in FP32, the precision these tables are kept in.
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
-                    uint16_t *occ_list, uint16_t *virt_list, uint32_t *occ_bits, float *G, float *AinvT,
-                    unsigned *status) {
+                    uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, float *G,
+                    float *AinvT, unsigned *status) {
     const int w = blockIdx.x, sg = blockIdx.y;
     const int n = sg ? nb : na, nv = M - n;
     const int ne = na + nb, nw = (M + 31) / 32;
@@ -241,7 +248,14 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         B[x * ld + c] = C[(size_t)s_occ[c] * n + x];
     }
     __syncthreads();
-    for (int s = tid; s < nv; s += nt) vl[s] = s_virt[s];
+    {
+        uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)sg * M;
+        for (int s = tid; s < nv; s += nt) {
+            vl[s] = s_virt[s];
+            pw[s_virt[s]] = (uint16_t)(0x8000 | s);
+        }
+        for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
+    }
     // ---- LU with partial pivoting, FP64: P B = L U (L unit lower, stored below the diagonal)
     for (int k = 0; k < n; ++k) {
         if (warp == 0) {
@@ -462,14 +476,14 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
         e = cudaFuncSetAttribute(k_init_tables<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             k_init_tables<double><<<grid, VMC_THREADS, smem, ctx->stream>>>(
-                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
+                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
                 (double *)Wk->G, (double *)Wk->AinvT, ctx->d_status);
     } else {
         const size_t smem_m = sizeof(double) * (size_t)nmax * (nmax + 1) * 2 + 16;
         e = cudaFuncSetAttribute(k_init_tables_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         if (e == cudaSuccess)
             k_init_tables_mixed<<<grid, VMC_THREADS, smem_m, ctx->stream>>>(
-                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->occ_bits,
+                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
                 (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status);
     }
     ctx->launches += 1;

@@ -30,7 +30,7 @@ class vmc_walkers(ct.Structure):
     _fields_ = [("W", ct.c_int), ("M", ct.c_int), ("n_alpha", ct.c_int), ("n_beta", ct.c_int),
                 ("precision", ct.c_int),
                 ("occ_bits", ct.c_void_p), ("occ_list", ct.c_void_p), ("virt_list", ct.c_void_p),
-                ("G", ct.c_void_p), ("AinvT", ct.c_void_p), ("S", ct.c_void_p), ("F", ct.c_void_p),
+                ("pos", ct.c_void_p), ("G", ct.c_void_p), ("AinvT", ct.c_void_p), ("S", ct.c_void_p), ("F", ct.c_void_p),
                 ("e_diag", ct.c_void_p), ("rng_counter", ct.c_void_p)]
 
 
@@ -143,7 +143,7 @@ def vmc_lists_info(lists):
 
 
 def vmc_walkers_sizes(W, M, na, nb, lists):
-    out = (ct.c_int64 * 9)()
+    out = (ct.c_int64 * 10)()
     _check(None, lib().vmc_walkers_sizes(W, M, na, nb, lists, out))
     return list(out)
 
@@ -209,6 +209,7 @@ class Walkers:
     occ_bits: torch.Tensor
     occ_list: torch.Tensor
     virt_list: torch.Tensor
+    pos: torch.Tensor
     G: torch.Tensor
     AinvT: torch.Tensor
     S: torch.Tensor
@@ -222,12 +223,13 @@ class Walkers:
         real = torch.float64 if precision == VMC_FP64 else torch.float32
         z = lambda k, dt: torch.zeros(max(1, n[k]), dtype=dt, device=device)
         return cls(W, M, na, nb, precision, z(0, torch.int32), z(1, torch.int16), z(2, torch.int16),
-                   z(3, real), z(4, real), z(5, real), z(6, torch.float64), z(7, torch.float64),
-                   z(8, torch.int64))
+                   z(3, torch.int16), z(4, real), z(5, real), z(6, real), z(7, torch.float64),
+                   z(8, torch.float64), z(9, torch.int64))
 
     def struct(self) -> vmc_walkers:
         return vmc_walkers(self.W, self.M, self.n_alpha, self.n_beta, self.precision,
-                           _ptr(self.occ_bits), _ptr(self.occ_list), _ptr(self.virt_list), _ptr(self.G),
+                           _ptr(self.occ_bits), _ptr(self.occ_list), _ptr(self.virt_list), _ptr(self.pos),
+                           _ptr(self.G),
                            _ptr(self.AinvT), _ptr(self.S), _ptr(self.F), _ptr(self.e_diag),
                            _ptr(self.rng_counter))
 
