@@ -43,8 +43,8 @@ struct ListsView {
     int cpr;       // warp chunks (32 candidates) per spin-orbital row
     int n_groups;  // singles blocks of 32 spin orbitals + 2M * cpr row chunks
     int64_t ns, nds, ndo;
-    // singles, CSR over spatial i; records: mixed {a, w_alpha, w_beta, 0} (16 B),
-    // FP64 {a, 0, w_alpha, w_beta} (32 B, the first 8 bytes hold a)
+    // singles, CSR over spatial i; records {a, w_alpha, w_beta, 0}: 16 B (mixed) or 32 B (FP64,
+    // the first 8 bytes hold a)
     const uint32_t *s_off, *s_len, *s_owner;
     const uint16_t *s_a;
     const float4 *s_rec32;

@@ -180,7 +180,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     auto bits_f = [](uint32_t u) { float f; memcpy(&f, &u, 4); return f; };
     for (int64_t e = 0; e < ns; ++e) {
         s_r32[e] = make_float4(bits_f(s_a[e]), 1.0f, 1.0f, 0.0f);
-        s_r64[e] = make_double4_32a(bits_d(s_a[e]), 0.0, 1.0, 1.0);
+        s_r64[e] = make_double4_32a(bits_d(s_a[e]), 1.0, 1.0, 0.0);
     }
     for (int64_t e = 0; e < nds; ++e) {
         ds_r32[e] = make_float4(bits_f(ds_ab[e]), (float)ds_vd[e], 1.0f, 1.0f);
@@ -332,7 +332,7 @@ __global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J) {
             const int I = sg * M + (int)L.s_owner[e], A = sg * M + L.s_a[e];
             lw = -jget(J, N2, A, I) + jget(J, N2, A, A) - jget(J, N2, I, I);
             const double w = exp(lw);
-            ((double *)&L.s_rec64[e])[2 + sg] = w;
+            ((double *)&L.s_rec64[e])[1 + sg] = w;
             ((float *)&L.s_rec32[e])[1 + sg] = (float)w;
             continue;
         }
