@@ -368,3 +368,13 @@ def test_singles_screen_uses_two_electron_bound():
     assert n_single_kept > 0
     el, _, _ = Oracle(sys, prm).local_energy_batch(n, eps)
     np.testing.assert_allclose(el, el_ref, rtol=1e-10, atol=1e-10)
+
+
+def test_golden_constants_are_used_consistently():
+    """The constants tests rely on match tests/golden/paper_values.json (each cited there)."""
+    import json
+    from pathlib import Path
+    g = json.loads((Path(__file__).parent / "golden" / "paper_values.json").read_text())
+    d = g["amsgrad_defaults"]
+    assert (d["alpha"], d["beta1"], d["beta2"]) == (0.01, 0.1, 0.01)
+    assert abs(g["free_fermion_ring10_energy"]["value"] + 4.0 * (1.0 + math.sqrt(5.0))) < 1e-12
