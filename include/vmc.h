@@ -234,6 +234,21 @@ vmc_status vmc_energy_gradient(vmc_ctx *ctx, size_t n, const double *d_sums, con
 vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const double *d_e_loc,
                              double *d_out);
 
+/*
+ * vmc_grad_logpsi without any allocation and without a context (the paper has no counterpart;
+ * it serves callers that may not allocate device memory: code running during CUDA-graph stream
+ * capture, or deployments whose device memory is owned by another allocator or fixed up front).
+ * Computes the same sums as vmc_grad_logpsi (accumulated into d_dJ, d_dC_alpha, d_dC_beta) for
+ * weights d_w [W], using a library-owned 16 MiB device scratch array instead of a workspace.
+ * Limit: 256 + 8 W (rounded up to 256 B) + max(64 M^2, 16 M n_max) bytes must fit in 16 MiB,
+ * and n_max <= 128; otherwise VMC_ERR_ARG.  The first call on a device looks up the scratch
+ * array's address (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.  Work is queued on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ */
+vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w, double *d_dJ,
+                                   double *d_dC_alpha, double *d_dC_beta, void *cuda_stream);
+
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */
 uint64_t vmc_launch_count(const vmc_ctx *ctx);
 

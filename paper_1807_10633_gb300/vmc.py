@@ -70,6 +70,7 @@ def lib() -> ct.CDLL:
             "vmc_energy_gradient": ([P, ct.c_size_t, P, P, P, P], I),
             "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
+            "vmc_grad_logpsi_noalloc": ([ct.POINTER(vmc_walkers), P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -191,6 +192,14 @@ def vmc_accumulate_gradient(ctx, walkers, t_res, e_loc, AO, AEO, sums):
 
 def vmc_energy_gradient(ctx, sums, A_O, A_EO, g):
     _check(ctx, lib().vmc_energy_gradient(ctx, g.numel(), _ptr(sums), _ptr(A_O), _ptr(A_EO), _ptr(g)))
+
+
+def vmc_grad_logpsi_noalloc(walkers, w, dJ, dCa, dCb, stream=None):
+    """Context-free, allocation-free variant of vmc_grad_logpsi (see include/vmc.h)."""
+    s = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else (stream or 0)
+    st = lib().vmc_grad_logpsi_noalloc(ct.byref(walkers), _ptr(w), _ptr(dJ), _ptr(dCa), _ptr(dCb), s)
+    if st != 0:
+        raise VmcError(st, "vmc_grad_logpsi_noalloc")
 
 
 def vmc_launch_count(ctx) -> int:
