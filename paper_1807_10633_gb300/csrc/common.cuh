@@ -77,6 +77,8 @@ struct vmc_lists {
     void *dev = nullptr;     // one device allocation holding every array
     size_t dev_bytes = 0;
     ListsView view{};
+    void *cf = nullptr;      // FP32 copy of C_alpha | C_beta (M x 2M floats at most)
+    void *jsym = nullptr;    // symmetric copies of J: FP64 (2M)^2 then FP32 (2M)^2
     const double *jastrow_for = nullptr;   // J pointer the constants were refreshed for
     uint64_t jastrow_epoch = 0;
 };

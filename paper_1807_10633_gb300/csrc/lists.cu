@@ -241,6 +241,8 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     const size_t i_Kd = add(Kd.data(), sizeof(double) * MM * MM);
     const size_t i_hd = add(hd.data(), sizeof(double) * MM);
     const size_t i_h1 = add(h1, sizeof(double) * MM * MM);
+    const size_t i_cf = add(nullptr, sizeof(float) * MM * 2 * MM);
+    const size_t i_jsym = add(nullptr, (sizeof(double) + sizeof(float)) * 4 * MM * MM);
 
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce == cudaSuccess) ce = cudaMalloc(&L->dev, off);
@@ -290,6 +292,8 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     v.Tj = (const double *)P(i_Tj); v.Tjk = (const double *)P(i_Tjk);
     v.Jd = (const double *)P(i_Jd); v.Kd = (const double *)P(i_Kd);
     v.hd = (const double *)P(i_hd); v.h1 = (const double *)P(i_h1);
+    L->cf = P(i_cf);
+    L->jsym = P(i_jsym);
     // the Jastrow constants are written by the first walker (re)initialisation
     vmc_status st = lists_set_eps(ctx, L, eps);
     if (st != VMC_OK) { vmc_lists_destroy(L); return st; }
@@ -320,8 +324,14 @@ extern "C" vmc_status vmc_lists_info(const vmc_lists *L, int64_t *ns, int64_t *n
 //   w = exp(-J_ai - J_aj - J_bi - J_bj + J_ab + J_ij + d_a + d_b - d_i - d_j)   (doubles)
 //   w = exp(-J_ai + d_a - d_i)                                                   (singles)
 // with S_p = sum_{k occ, k != p} J_pk and d_p = J_pp.  These w are stored with every list entry.
-__global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J) {
+__global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J, double *__restrict__ js64,
+                                  float *__restrict__ js32) {
     const int M = L.M, N2 = 2 * M;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N2 * N2; t += gridDim.x * blockDim.x) {
+        const double v = jget(J, N2, t / N2, t % N2);   // symmetric copies for row-wise reads
+        js64[t] = v;
+        js32[t] = (float)v;
+    }
     const int64_t tot = 2 * L.ns + 2 * L.nds + L.ndo;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -368,10 +378,11 @@ __global__ void k_refresh_jastrow(ListsView L, const double *__restrict__ J) {
 }
 
 vmc_status launch_refresh_jastrow(vmc_ctx *ctx, vmc_lists *L, const double *J) {
-    const int64_t tot = 2 * L->ns + 2 * L->nds + L->ndo;
-    if (tot == 0) return VMC_OK;
+    const int64_t tot = std::max<int64_t>(2 * L->ns + 2 * L->nds + L->ndo, 4 * (int64_t)L->M * L->M);
     int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
-    k_refresh_jastrow<<<blocks, 256, 0, ctx->stream>>>(L->view, J);
+    double *js64 = (double *)L->jsym;
+    float *js32 = (float *)(js64 + 4 * (size_t)L->M * L->M);
+    k_refresh_jastrow<<<blocks, 256, 0, ctx->stream>>>(L->view, J, js64, js32);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "k_refresh_jastrow");
 }

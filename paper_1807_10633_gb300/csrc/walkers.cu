@@ -201,24 +201,27 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
 
 // Mixed form: LU of C_occ^T with partial pivoting in FP64 (in shared memory), then the inverse
 // from the factors and G = C C_occ^-1 in FP32, the precision these tables are kept in.
+// Shared memory: one n x (n+1) FP64 buffer; after the factorisation it is reused as two FP32
+// n x (n+1) arrays (factors, inverse), so four CTAs fit on an SM.
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
-                    uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, float *G,
-                    float *AinvT, unsigned *status) {
+                    const float *__restrict__ Cf, uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all,
+                    uint32_t *occ_bits, float *G, float *AinvT, unsigned *status) {
     const int w = blockIdx.x, sg = blockIdx.y;
     const int n = sg ? nb : na, nv = M - n;
     const int ne = na + nb, nw = (M + 31) / 32;
     const double *C = sg ? Cb : Ca;
+    const float *Csf = Cf + (sg ? (size_t)M * na : 0);     // FP32 copy of C^sigma
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ double sm[];
     const int ld = n + 1;
     double *B = sm;                               // n x ld FP64: LU factors
-    float *LUf = (float *)(B + (size_t)n * ld);   // n x ld FP32 copy of the factors
-    float *Y = LUf + (size_t)n * ld;              // n x ld FP32: inverse being formed
+    float *LUf = (float *)sm;                     // n x ld FP32 (aliases B after the factorisation)
+    float *Y = LUf + (size_t)n * ld;              // n x ld FP32
     __shared__ uint16_t s_occ[VMC_MAX_M], s_virt[VMC_MAX_M];
     __shared__ uint8_t mark[VMC_MAX_M];
     __shared__ int perm[VMC_MAX_M];
-    __shared__ int s_piv, s_sing;
+    __shared__ int s_sing;
     const uint16_t *occ = occ_list + (size_t)w * ne + (sg ? na : 0);
     uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
     for (int k = tid; k < M; k += nt) mark[k] = 0;
@@ -256,7 +259,8 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         }
         for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
     }
-    // ---- LU with partial pivoting, FP64: P B = L U (L unit lower, stored below the diagonal)
+    // ---- LU with partial pivoting, FP64: P B = L U.  Per column: warp 0 finds the pivot, swaps
+    //      the rows and scales the multipliers; then all threads update the trailing block.
     for (int k = 0; k < n; ++k) {
         if (warp == 0) {
             double best = -1.0;
@@ -271,26 +275,23 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
                 const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
                 if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
             }
-            if (lane == 0) {
-                s_piv = idx;
-                if (idx != k) { const int t = perm[k]; perm[k] = perm[idx]; perm[idx] = t; }
+            if (idx != k) {
+                for (int c = lane; c < n; c += 32) {
+                    const double t = B[k * ld + c];
+                    B[k * ld + c] = B[idx * ld + c];
+                    B[idx * ld + c] = t;
+                }
+                if (lane == 0) { const int t = perm[k]; perm[k] = perm[idx]; perm[idx] = t; }
             }
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != k)
-            for (int c = tid; c < n; c += nt) {
-                const double t = B[k * ld + c];
-                B[k * ld + c] = B[p * ld + c];
-                B[p * ld + c] = t;
+            __syncwarp();
+            double d = B[k * ld + k];
+            if (d == 0.0) {
+                if (lane == 0) s_sing = 1;
+                d = 1.0;
             }
-        __syncthreads();
-        double d = B[k * ld + k];
-        if (d == 0.0) {
-            if (tid == 0) s_sing = 1;
-            d = 1.0;
+            const double dinv = 1.0 / d;
+            for (int r = k + 1 + lane; r < n; r += 32) B[r * ld + k] *= dinv;
         }
-        for (int r = k + 1 + tid; r < n; r += nt) B[r * ld + k] /= d;
         __syncthreads();
         const int m = n - k - 1;
         for (int t = tid; t < m * m; t += nt) {
@@ -300,18 +301,26 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         __syncthreads();
     }
     if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
-    // ---- FP32 inverse from the factors: Y = P (rows), then L^-1, then U^-1
-    for (int t = tid; t < n * n; t += nt) {
-        const int r = t / n, c = t % n;
-        LUf[r * ld + c] = (float)B[r * ld + c];
+    // ---- FP32 copies: unit-lower L, unit-upper U' = D^-1 U, and 1/D; the buffer is reused
+    {
+        const int per = (n * n + nt - 1) / nt;
+        float vals[(VMC_MAX_M / 2 + 1) * (VMC_MAX_M / 2 + 1) / VMC_THREADS + 2];
+        int cnt = 0;
+        for (int t = tid; t < n * n && cnt < per; t += nt, ++cnt) {
+            const int r = t / n, c = t % n;
+            const double v = B[r * ld + c];
+            vals[cnt] = c > r ? (float)(v / B[r * ld + r]) : (c == r ? (float)(1.0 / v) : (float)v);
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int t = tid; t < n * n && cnt < per; t += nt, ++cnt) {
+            const int r = t / n, c = t % n;
+            LUf[r * ld + c] = vals[cnt];
+            Y[r * ld + c] = perm[r] == c ? 1.0f : 0.0f;      // rows of the permutation
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int t = tid; t < n * n; t += nt) {   // (P B)^-1 = U^-1 L^-1 P: start from the rows of P
-        const int r = t / n, c = t % n;
-        Y[r * ld + c] = perm[r] == c ? 1.0f : 0.0f;
-    }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {             // forward: L (unit diagonal)
+    for (int k = 0; k < n - 1; ++k) {             // forward: L (unit diagonal)
         const int m = n - k - 1;
         for (int t = tid; t < m * n; t += nt) {
             const int r = k + 1 + t / n, c = t % n;
@@ -319,10 +328,12 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         }
         __syncthreads();
     }
-    for (int k = n - 1; k >= 0; --k) {        // backward: U
-        const float dk = LUf[k * ld + k] == 0.0f ? 1.0f : LUf[k * ld + k];
-        for (int c = tid; c < n; c += nt) Y[k * ld + c] /= dk;
-        __syncthreads();
+    for (int t = tid; t < n * n; t += nt) {       // D^-1
+        const int r = t / n, c = t % n;
+        Y[r * ld + c] *= LUf[r * ld + r];
+    }
+    __syncthreads();
+    for (int k = n - 1; k > 0; --k) {             // backward: U' (unit diagonal)
         for (int t = tid; t < k * n; t += nt) {
             const int r = t / n, c = t % n;
             Y[r * ld + c] -= LUf[r * ld + k] * Y[k * ld + c];
@@ -337,19 +348,45 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         const int c = t / n, x = t % n;
         AinvT[aofs + t] = Y[c * ld + x];
     }
-    for (int t = tid; t < nv * n; t += nt) {
-        const int s = t / n, c = t % n;
-        const double *crow = C + (size_t)s_virt[s] * n;
-        float acc = 0.0f;
-        for (int x = 0; x < n; ++x) acc = fmaf((float)crow[x], Y[c * ld + x], acc);
-        G[gofs + t] = acc;
+    // G[s][c] = sum_x C[virt[s]][x] AinvT[c][x]: 4 x 4 register tiles (slots x columns)
+    const int ts = (nv + 3) / 4, tc = (n + 3) / 4;
+    for (int tile = tid; tile < ts * tc; tile += nt) {
+        const int s0 = (tile / tc) * 4, c0 = (tile % tc) * 4;
+        float acc[4][4] = {};
+        const float *cr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cr[i] = Csf + (size_t)s_virt[min(s0 + i, nv - 1)] * n;
+        for (int x = 0; x < n; ++x) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = __ldg(cr[i] + x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Y[min(c0 + j, n - 1) * ld + x];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (s0 + i < nv && c0 + j < n) G[gofs + (size_t)(s0 + i) * n + c0 + j] = acc[i][j];
     }
+}
+
+__global__ void k_convert_c(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
+                            float *__restrict__ Cf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nA = M * na;
+    if (t < nA) Cf[t] = (float)Ca[t];
+    else if (t < nA + M * nb) Cf[t] = (float)Cb[t - nA];
 }
 
 // Jastrow sums S_p, and (full init only) Fock sums and the diagonal energy.
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
-k_init_sums(ListsView L, int na, int nb, const double *__restrict__ J, const uint16_t *occ_list,
+k_init_sums(ListsView L, int na, int nb, const real *__restrict__ Jsym, const uint16_t *occ_list,
             real *S, double *F, double *e_diag, int full) {
     const int w = blockIdx.x, M = L.M, N2 = 2 * M, ne = na + nb;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -358,13 +395,14 @@ k_init_sums(ListsView L, int na, int nb, const double *__restrict__ J, const uin
     const uint16_t *occ = occ_list + (size_t)w * ne;
     for (int c = tid; c < ne; c += nt) s_so[c] = (c < na ? 0 : M) + occ[c];
     __syncthreads();
+    // S_p = sum_{k occ, k != p} J_kp: rows of the symmetric copy, coalesced over p
     for (int p = tid; p < N2; p += nt) {
-        double acc = 0.0;
+        real acc = 0;
         for (int c = 0; c < ne; ++c) {
             const int k = s_so[c];
-            if (k != p) acc += jget(J, N2, p, k);
+            if (k != p) acc += Jsym[(size_t)k * N2 + p];
         }
-        S[(size_t)w * N2 + p] = (real)acc;
+        S[(size_t)w * N2 + p] = acc;
     }
     if (!full) return;
     // F[s][e] = h_ai + sum_{j occ, spin s} Tjk[j][e] + sum_{j occ, other spin} Tj[j][e]
@@ -479,22 +517,27 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
                 M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
                 (double *)Wk->G, (double *)Wk->AinvT, ctx->d_status);
     } else {
-        const size_t smem_m = sizeof(double) * (size_t)nmax * (nmax + 1) * 2 + 16;
+        const size_t smem_m = sizeof(double) * (size_t)nmax * (nmax + 1) + 16;
+        float *Cf = (float *)L->cf;
+        k_convert_c<<<(M * (na + nb) + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, P->C_alpha, P->C_beta, Cf);
+        ctx->launches += 1;
         e = cudaFuncSetAttribute(k_init_tables_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         if (e == cudaSuccess)
             k_init_tables_mixed<<<grid, VMC_THREADS, smem_m, ctx->stream>>>(
-                M, na, nb, P->C_alpha, P->C_beta, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
+                M, na, nb, P->C_alpha, P->C_beta, Cf, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
                 (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status);
     }
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(ctx, e, "k_init_tables");
+    const double *js64 = (const double *)L->jsym;
+    const float *js32 = (const float *)(js64 + 4 * (size_t)M * M);
     if (Wk->precision == VMC_FP64)
         k_init_sums<double><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
-            L->view, na, nb, P->J, Wk->occ_list, (double *)Wk->S, Wk->F, Wk->e_diag, full);
+            L->view, na, nb, js64, Wk->occ_list, (double *)Wk->S, Wk->F, Wk->e_diag, full);
     else
         k_init_sums<float><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
-            L->view, na, nb, P->J, Wk->occ_list, (float *)Wk->S, Wk->F, Wk->e_diag, full);
+            L->view, na, nb, js32, Wk->occ_list, (float *)Wk->S, Wk->F, Wk->e_diag, full);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "k_init_sums");
 }
