@@ -344,20 +344,111 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
 }
 
 // ---------------------------------------------------------------------------------- CTMC
+// Selection: one warp per walker.  Scans the walker's group sums (u128), draws Philox, finds the
+// group whose prefix crosses T and re-walks only that group with the same entry code as the
+// local-energy kernel.  Writes the move code (0 = no move) and advances the walker's counter.
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
-k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 *__restrict__ rates,
-            uint64_t seed, uint64_t *__restrict__ move_code, unsigned *status) {
+k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_t seed,
+              uint64_t *__restrict__ move_code, unsigned *status) {
+    const Geo geo = make_geo(A.M, A.na, A.nb);
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= A.W) return;
+    const int M = geo.M, N2 = 2 * M, n_groups = L.n_groups;
+    const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
+    const real *Sw = (const real *)A.S + (size_t)w * N2;
+    const u128 *R = rates + (size_t)w * n_groups;
+    const int per = (n_groups + 31) / 32;
+    const int g0 = lane * per, g1 = min(n_groups, g0 + per);
+    u128 seg = 0;
+    for (int g = g0; g < g1; ++g) seg += R[g];
+    const u128 incl = warp_incl_scan_u128(seg, lane);
+    const u128 Q = shfl_u128(incl, 31);
+    const uint64_t U = philox4x64_word0(A.rng[w], 0, 0, 0, seed, (uint64_t)w);
+    const uint64_t qh = (uint64_t)(Q >> 64), ql = (uint64_t)Q;
+    const u128 T = (u128)U * qh + (u128)__umul64hi(U, ql);
+    const unsigned ball = __ballot_sync(0xffffffffu, incl > T);
+    int gsel = -1;
+    u128 before = 0;
+    if (Q != 0 && ball) {
+        const int src = __ffs(ball) - 1;
+        u128 pre = shfl_u128(incl - seg, src);
+        if (lane == src) {
+            for (int g = g0; g < g1; ++g) {
+                if (pre + R[g] > T) { gsel = g; break; }
+                pre += R[g];
+            }
+        }
+        gsel = __shfl_sync(0xffffffffu, gsel, src);
+        before = shfl_u128(pre, src);
+    }
+    uint64_t code = 0;
+    if (gsel >= 0) {
+        const u128 Tl = T - before;   // threshold inside the group
+        View<real> V;
+        V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
+        V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+        Unit<real> u;
+        const bool act = setup_unit<real>(L, V, gsel, lane, u);
+        unsigned mask = __ballot_sync(0xffffffffu, act);
+        u128 carry = 0;
+        unsigned flag = 0;
+        bool found = false;
+        while (mask && !found) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const Unit<real> v = shfl_unit(u, src);
+            for (uint32_t k0 = 0; k0 < v.len && !found; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                u128 q = 0;
+                int a = -1, b = -1;
+                if (k < v.len) {
+                    real ratio, contrib;
+                    if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
+                }
+                const u128 incl2 = warp_incl_scan_u128(q, lane) + carry;
+                const unsigned hit = __ballot_sync(0xffffffffu, k < v.len && q != 0 && incl2 > Tl);
+                if (hit) {
+                    const int h = __ffs(hit) - 1;
+                    uint64_t c = 0;
+                    if (lane == h) {
+                        const uint64_t kind = v.kind == 0 ? 1 : 2;
+                        const uint64_t j10 = kind == 2 ? (uint64_t)v.j : 1023ull, b10 = kind == 2 ? (uint64_t)b : 1023ull;
+                        c = kind | ((uint64_t)v.i << 2) | (j10 << 12) | ((uint64_t)a << 22) | (b10 << 32);
+                    }
+                    code = __shfl_sync(0xffffffffu, c, h);
+                    found = true;
+                }
+                carry = shfl_u128(incl2, 31);
+            }
+        }
+        if (!found && lane == 0) atomicOr(status, VMC_DEV_INCONSISTENT);
+    } else if (lane == 0) {
+        atomicOr(status, VMC_DEV_NOMOVE);
+    }
+    if (lane == 0) {
+        move_code[w] = code;
+        A.rng[w] += 1;
+    }
+}
+
+// Move update: one CTA per walker (Sec. III.B): diagonal energy, Jastrow sums, Fock sums, then the
+// rank-1 (singles, opposite-spin doubles) or rank-2 Woodbury (same-spin doubles) update of G and
+// AinvT, and the occupation lists, bits and orbital map.
+template <typename real>
+__global__ void __launch_bounds__(VMC_THREADS)
+k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint64_t *__restrict__ move_code) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    const int M = geo.M, ne = geo.ne, N2 = 2 * M, n_groups = L.n_groups;
+    const uint64_t code = move_code[w];
+    if (code == 0) return;
+    const int M = geo.M, ne = geo.ne, N2 = 2 * M;
     extern __shared__ __align__(16) unsigned char smraw[];
     uint16_t *pos = (uint16_t *)smraw;
     real *vec = (real *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15);
     // vec holds: ua[nmax], ub[nmax], gci[M], gcj[M], arow_i[nmax], arow_j[nmax]
-    __shared__ int s_move[6];       // kind, i, j, a, b, ok
     __shared__ double red[VMC_WARPS];
-
     real *Gw = (real *)A.G + (size_t)w * geo.g_stride;
     real *Aw = (real *)A.AinvT + (size_t)w * geo.a_stride;
     real *Sw = (real *)A.S + (size_t)w * N2;
@@ -367,88 +458,8 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
     uint16_t *posw = A.pos + (size_t)w * N2;
     for (int p = tid; p < N2; p += nt) pos[p] = posw[p];
     __syncthreads();
-
-    // ---- choose the group (warp 0), then the entry inside it
-    if (warp == 0) {
-        const u128 *R = rates + (size_t)w * n_groups;
-        const int per = (n_groups + 31) / 32;
-        const int g0 = lane * per, g1 = min(n_groups, g0 + per);
-        u128 seg = 0;
-        for (int g = g0; g < g1; ++g) seg += R[g];
-        const u128 incl = warp_incl_scan_u128(seg, lane);
-        const u128 Q = shfl_u128(incl, 31);
-        const uint64_t U = philox4x64_word0(A.rng[w], 0, 0, 0, seed, (uint64_t)w);
-        const uint64_t qh = (uint64_t)(Q >> 64), ql = (uint64_t)Q;
-        const u128 T = (u128)U * qh + (u128)__umul64hi(U, ql);
-        const unsigned ball = __ballot_sync(0xffffffffu, incl > T);
-        int gsel = -1;
-        u128 before = 0;
-        if (Q != 0 && ball) {
-            const int src = __ffs(ball) - 1;
-            u128 pre = shfl_u128(incl - seg, src);
-            if (lane == src) {
-                for (int g = g0; g < g1; ++g) {
-                    if (pre + R[g] > T) { gsel = g; break; }
-                    pre += R[g];
-                }
-            }
-            gsel = __shfl_sync(0xffffffffu, gsel, src);
-            before = shfl_u128(pre, src);
-        }
-        if (lane == 0) { s_move[0] = 0; s_move[5] = 0; }
-        __syncwarp();
-        if (gsel >= 0) {
-            const u128 Tl = T - before;   // threshold inside the group
-            View<real> V;
-            V.pos = pos; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
-            V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
-            Unit<real> u;
-            const bool act = setup_unit<real>(L, V, gsel, lane, u);
-            unsigned mask = __ballot_sync(0xffffffffu, act);
-            u128 carry = 0;
-            unsigned flag = 0;
-            bool found = false;
-            while (mask && !found) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const Unit<real> v = shfl_unit(u, src);
-                for (uint32_t k0 = 0; k0 < v.len && !found; k0 += 32) {
-                    const uint32_t k = k0 + lane;
-                    u128 q = 0;
-                    int a = -1, b = -1;
-                    if (k < v.len) {
-                        real ratio, contrib;
-                        if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
-                    }
-                    const u128 incl2 = warp_incl_scan_u128(q, lane) + carry;
-                    const unsigned hit = __ballot_sync(0xffffffffu, k < v.len && q != 0 && incl2 > Tl);
-                    if (hit) {
-                        const int h = __ffs(hit) - 1;
-                        if (lane == h) {
-                            s_move[0] = v.kind == 0 ? 1 : 2;
-                            s_move[1] = v.i; s_move[2] = v.j; s_move[3] = a; s_move[4] = b; s_move[5] = 1;
-                        }
-                        found = true;
-                    }
-                    carry = shfl_u128(incl2, 31);
-                }
-            }
-            if (!found && lane == 0) atomicOr(status, VMC_DEV_INCONSISTENT);
-        } else if (lane == 0) {
-            atomicOr(status, VMC_DEV_NOMOVE);
-        }
-    }
-    __syncthreads();
-    const int ok = s_move[5];
-    if (!ok) {
-        if (tid == 0) { move_code[w] = 0; A.rng[w] += 1; }
-        return;
-    }
-    const int kind = s_move[0], I = s_move[1], Jo = s_move[2], Ao = s_move[3], Bo = s_move[4];
-    if (tid == 0) {
-        const uint64_t j10 = kind == 2 ? (uint64_t)Jo : 1023ull, b10 = kind == 2 ? (uint64_t)Bo : 1023ull;
-        move_code[w] = (uint64_t)kind | ((uint64_t)I << 2) | (j10 << 12) | ((uint64_t)Ao << 22) | (b10 << 32);
-    }
+    const int kind = (int)(code & 3), I = (int)((code >> 2) & 1023), Jo = (int)((code >> 12) & 1023);
+    const int Ao = (int)((code >> 22) & 1023), Bo = (int)((code >> 32) & 1023);
 
     // ---- diagonal energy change (old occupation), FP64
     {
@@ -580,7 +591,6 @@ k_ctmc_step(ListsView L, WalkerArgs A, const double *__restrict__ J, const u128 
             }
         }
     }
-    if (tid == 0) A.rng[w] += 1;
 }
 
 }  // namespace
@@ -630,19 +640,22 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const size_t smem = 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
     WalkerArgs A = make_args(Wk);
+    const int sel_blocks = (Wk->W + VMC_WARPS - 1) / VMC_WARPS;
     cudaError_t e;
     if (Wk->precision == VMC_FP64) {
-        e = cudaFuncSetAttribute(k_ctmc_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ctmc_select<double><<<sel_blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, rates, seed, move_code,
+                                                                           ctx->d_status);
+        e = cudaFuncSetAttribute(k_ctmc_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_ctmc_step<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, seed,
-                                                                           move_code, ctx->d_status);
+            k_ctmc_apply<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, move_code);
     } else {
-        e = cudaFuncSetAttribute(k_ctmc_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ctmc_select<float><<<sel_blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, rates, seed, move_code,
+                                                                          ctx->d_status);
+        e = cudaFuncSetAttribute(k_ctmc_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_ctmc_step<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, rates, seed,
-                                                                          move_code, ctx->d_status);
+            k_ctmc_apply<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, move_code);
     }
-    ctx->launches += 1;
+    ctx->launches += 2;
     if (e == cudaSuccess) e = cudaGetLastError();
-    return cuda_check(ctx, e, "k_ctmc_step");
+    return cuda_check(ctx, e, "k_ctmc_select/k_ctmc_apply");
 }

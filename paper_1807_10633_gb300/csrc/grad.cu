@@ -10,8 +10,8 @@
 
 namespace {
 
-constexpr int kChunkJ = 1024;   // walkers per CTA for dJ
-constexpr int kChunkC = 256;    // walkers per CTA for dC
+constexpr int kChunkJ = 256;    // walkers per CTA for dJ
+constexpr int kChunkC = 64;     // walkers per CTA for dC
 constexpr int kRowsC = 16;      // orbital rows per CTA (registers per thread) for dC
 
 // 32 consecutive spin-orbital occupation bits starting at spin orbital p0 (lane l -> bit l)

@@ -57,12 +57,13 @@ __device__ void gj_invert(double *B, double *X, int n, int ld, double *colk, int
         }
         for (int r = tid; r < n; r += nt) colk[r] = B[r * ld + k];
         __syncthreads();
-        for (int t = tid; t < n * 2 * n; t += nt) {
-            const int r = t / (2 * n), c = t % (2 * n);
+        for (int r = warp; r < n; r += (nt >> 5)) {     // rows over warps, columns over lanes
             if (r == k) continue;
             const double f = colk[r];
-            if (c < n) B[r * ld + c] -= f * B[k * ld + c];
-            else X[r * ld + (c - n)] -= f * X[k * ld + (c - n)];
+            for (int c = lane; c < n; c += 32) {
+                B[r * ld + c] -= f * B[k * ld + c];
+                X[r * ld + c] -= f * X[k * ld + c];
+            }
         }
         __syncthreads();
     }
@@ -293,10 +294,9 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
             for (int r = k + 1 + lane; r < n; r += 32) B[r * ld + k] *= dinv;
         }
         __syncthreads();
-        const int m = n - k - 1;
-        for (int t = tid; t < m * m; t += nt) {
-            const int r = k + 1 + t / m, c = k + 1 + t % m;
-            B[r * ld + c] -= B[r * ld + k] * B[k * ld + c];
+        for (int r = k + 1 + warp; r < n; r += (nt >> 5)) {
+            const double l = B[r * ld + k];
+            for (int c = k + 1 + lane; c < n; c += 32) B[r * ld + c] -= l * B[k * ld + c];
         }
         __syncthreads();
     }
@@ -320,23 +320,23 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         }
         __syncthreads();
     }
+    const int nwarp = nt >> 5;
     for (int k = 0; k < n - 1; ++k) {             // forward: L (unit diagonal)
-        const int m = n - k - 1;
-        for (int t = tid; t < m * n; t += nt) {
-            const int r = k + 1 + t / n, c = t % n;
-            Y[r * ld + c] -= LUf[r * ld + k] * Y[k * ld + c];
+        for (int r = k + 1 + warp; r < n; r += nwarp) {
+            const float l = LUf[r * ld + k];
+            for (int c = lane; c < n; c += 32) Y[r * ld + c] -= l * Y[k * ld + c];
         }
         __syncthreads();
     }
-    for (int t = tid; t < n * n; t += nt) {       // D^-1
-        const int r = t / n, c = t % n;
-        Y[r * ld + c] *= LUf[r * ld + r];
+    for (int r = warp; r < n; r += nwarp) {       // D^-1
+        const float d = LUf[r * ld + r];
+        for (int c = lane; c < n; c += 32) Y[r * ld + c] *= d;
     }
     __syncthreads();
     for (int k = n - 1; k > 0; --k) {             // backward: U' (unit diagonal)
-        for (int t = tid; t < k * n; t += nt) {
-            const int r = t / n, c = t % n;
-            Y[r * ld + c] -= LUf[r * ld + k] * Y[k * ld + c];
+        for (int r = warp; r < k; r += nwarp) {
+            const float u = LUf[r * ld + k];
+            for (int c = lane; c < n; c += 32) Y[r * ld + c] -= u * Y[k * ld + c];
         }
         __syncthreads();
     }
