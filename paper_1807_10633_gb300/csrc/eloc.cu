@@ -88,7 +88,7 @@ struct Unit {
     int cls;       // spin for kinds 0 and 1
     int ci, cj;    // columns of i and j
     int i, j;      // spin orbitals
-    real einv;     // 1 / (E_i E_j)   (1 / E_i for singles)
+    real einv;     // (1/E_i)(1/E_j)   (1/E_i for singles)
 };
 
 // Shared-memory view of one walker used by the entry evaluation.
@@ -101,10 +101,12 @@ struct View {
         return s ? Gb + (size_t)slot * ldb : Ga + (size_t)slot * lda;
     }
     const real *E;         // [2M] exp(S) (nullptr: compute from S on the fly)
+    const real *Einv;      // [2M] 1/exp(S) (with E)
     const real *S;         // walker S in global (used when E == nullptr)
     const double *F;       // walker F [2][ns]
     Geo geo;
     __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }
+    __device__ real Eiv(int p) const { return E ? Einv[p] : rrcp(rexp(S[p])); }
     __device__ bool occ(int p) const { return !(pos[p] & 0x8000); }
 };
 
@@ -135,7 +137,7 @@ __device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> 
         u.kind = 0; u.cls = s; u.i = i; u.j = -1;
         u.base = L.s_off[pi]; u.len = L.s_len[pi];
         u.ci = V.pos[i]; u.cj = 0;
-        u.einv = rrcp(V.Ev(i));
+        u.einv = V.Eiv(i);
         return u.len > 0;
     }
     const int r = (g - Gs) / L.cpr, chunk = (g - Gs) - r * L.cpr;
@@ -158,7 +160,7 @@ __device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> 
         u.base = L.do_off[tt]; u.len = L.do_len[tt];
     }
     if (u.len == 0) return false;
-    u.einv = rrcp(rmul(V.Ev(i), V.Ev(j)));
+    u.einv = rmul(V.Eiv(i), V.Eiv(j));
     return true;
 }
 
@@ -242,6 +244,13 @@ __device__ __forceinline__ u128 rate_of(real ratio, unsigned *flag) {
 template <typename real> struct AccT { typedef double type; };
 template <> struct AccT<float> { typedef float type; };
 
+__device__ __forceinline__ double warp_sum_acc(double v) { return warp_sum_f64(v); }
+__device__ __forceinline__ double warp_sum_acc(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return (double)v;
+}
+
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
@@ -254,7 +263,8 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
     real *sGa = (real *)smraw;
     real *sGb = sGa + (size_t)geo.nv_a * lda;
     real *sE = sGb + (size_t)geo.nv_b * ldb;
-    double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
+    real *sEi = sE + 2 * M;
+    double *eg = (double *)(((uintptr_t)(sEi + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
     uint16_t *pos = (uint16_t *)(eg + n_groups);
     __shared__ u128 red_q[VMC_WARPS];
     __shared__ int next_group;
@@ -274,7 +284,11 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
             }
         }
         const real *Sw = (const real *)A.S + (size_t)w * 2 * M;
-        for (int p = tid; p < 2 * M; p += nt) sE[p] = rexp(Sw[p]);
+        for (int p = tid; p < 2 * M; p += nt) {
+            const real e = rexp(Sw[p]);
+            sE[p] = e;
+            sEi[p] = rrcp(e);
+        }
         const uint16_t *pw = A.pos + (size_t)w * 2 * M;
         for (int p = tid; p < 2 * M; p += nt) pos[p] = pw[p];
         if (tid == 0) next_group = VMC_WARPS;
@@ -283,7 +297,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
 
     View<real> V;
     V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
-    V.E = sE; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+    V.E = sE; V.Einv = sEi; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
     typedef typename AccT<real>::type acc_t;
     u128 q_tot = 0;
     unsigned flag = 0;
@@ -309,7 +323,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
                 }
             }
         }
-        const double eg_sum = warp_sum_f64((double)e_grp);
+        const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
         if (lane == 0) {
             rates[(size_t)w * n_groups + g] = q_grp;
@@ -388,7 +402,7 @@ k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_
         const u128 Tl = T - before;   // threshold inside the group
         View<real> V;
         V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
-        V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+        V.E = nullptr; V.Einv = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, gsel, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -612,7 +626,7 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
+    const size_t smem = esz * (gpad + 4 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e;

@@ -384,26 +384,55 @@ __global__ void k_convert_c(int M, int na, int nb, const double *__restrict__ Ca
 }
 
 // Jastrow sums S_p, and (full init only) Fock sums and the diagonal energy.
+// Jastrow sums S_p = sum_{k occ, k != p} J_kp for a block of kSumWalkers walkers: each row of the
+// symmetric J copy is read once per block and added to every walker that occupies that orbital.
+// (Full init only:) Fock sums F and the diagonal energy, one walker per block.
+constexpr int kSumWalkers = 8;
+
+template <typename real>
+__global__ void __launch_bounds__(VMC_THREADS)
+k_jastrow_sums(int W, int M, const real *__restrict__ Jsym, const uint32_t *__restrict__ occ_bits, real *S) {
+    const int N2 = 2 * M, nw = (M + 31) / 32, w0 = blockIdx.x * kSumWalkers;
+    __shared__ uint32_t bits[kSumWalkers][2 * (VMC_MAX_M / 32)];
+    for (int t = threadIdx.x; t < kSumWalkers * 2 * nw; t += blockDim.x) {
+        const int k = t / (2 * nw), q = t % (2 * nw);
+        bits[k][q] = (w0 + k < W) ? occ_bits[(size_t)(w0 + k) * 2 * nw + q] : 0u;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+        real acc[kSumWalkers];
+#pragma unroll
+        for (int k = 0; k < kSumWalkers; ++k) acc[k] = 0;
+        for (int r = 0; r < N2; ++r) {
+            const int s = r >= M, kk = r - s * M;
+            const real j = Jsym[(size_t)r * N2 + p];
+#pragma unroll
+            for (int k = 0; k < kSumWalkers; ++k)
+                if ((bits[k][s * nw + (kk >> 5)] >> (kk & 31)) & 1u) acc[k] += j;
+        }
+        const real jd = Jsym[(size_t)p * N2 + p];
+        const int sp = p >= M, kp = p - sp * M;
+#pragma unroll
+        for (int k = 0; k < kSumWalkers; ++k) {
+            if (w0 + k >= W) break;
+            const bool occp = (bits[k][sp * nw + (kp >> 5)] >> (kp & 31)) & 1u;
+            S[(size_t)(w0 + k) * N2 + p] = occp ? acc[k] - jd : acc[k];
+        }
+    }
+}
+
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_sums(ListsView L, int na, int nb, const real *__restrict__ Jsym, const uint16_t *occ_list,
             real *S, double *F, double *e_diag, int full) {
-    const int w = blockIdx.x, M = L.M, N2 = 2 * M, ne = na + nb;
+    const int w = blockIdx.x, M = L.M, ne = na + nb;
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_so[2 * VMC_MAX_M];   // occupied spin orbitals
     __shared__ double red[VMC_WARPS];
     const uint16_t *occ = occ_list + (size_t)w * ne;
     for (int c = tid; c < ne; c += nt) s_so[c] = (c < na ? 0 : M) + occ[c];
     __syncthreads();
-    // S_p = sum_{k occ, k != p} J_kp: rows of the symmetric copy, coalesced over p
-    for (int p = tid; p < N2; p += nt) {
-        real acc = 0;
-        for (int c = 0; c < ne; ++c) {
-            const int k = s_so[c];
-            if (k != p) acc += Jsym[(size_t)k * N2 + p];
-        }
-        S[(size_t)w * N2 + p] = acc;
-    }
+    (void)Jsym; (void)S;
     if (!full) return;
     // F[s][e] = h_ai + sum_{j occ, spin s} Tjk[j][e] + sum_{j occ, other spin} Tj[j][e]
     for (int64_t e = tid; e < L.ns; e += nt) {
@@ -532,14 +561,18 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
     if (e != cudaSuccess) return cuda_check(ctx, e, "k_init_tables");
     const double *js64 = (const double *)L->jsym;
     const float *js32 = (const float *)(js64 + 4 * (size_t)M * M);
+    const int sb = (Wk->W + kSumWalkers - 1) / kSumWalkers;
     if (Wk->precision == VMC_FP64)
-        k_init_sums<double><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
-            L->view, na, nb, js64, Wk->occ_list, (double *)Wk->S, Wk->F, Wk->e_diag, full);
+        k_jastrow_sums<double><<<sb, VMC_THREADS, 0, ctx->stream>>>(Wk->W, M, js64, Wk->occ_bits, (double *)Wk->S);
     else
-        k_init_sums<float><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
-            L->view, na, nb, js32, Wk->occ_list, (float *)Wk->S, Wk->F, Wk->e_diag, full);
+        k_jastrow_sums<float><<<sb, VMC_THREADS, 0, ctx->stream>>>(Wk->W, M, js32, Wk->occ_bits, (float *)Wk->S);
     ctx->launches += 1;
-    return cuda_check(ctx, cudaGetLastError(), "k_init_sums");
+    if (full) {
+        k_init_sums<double><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
+            L->view, na, nb, js64, Wk->occ_list, nullptr, Wk->F, Wk->e_diag, 1);
+        ctx->launches += 1;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "k_jastrow_sums/k_init_sums");
 }
 
 vmc_status launch_log_psi(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_params *P, double *out) {
