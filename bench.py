@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="walkers in the oracle sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     return ap.parse_args()
 
 
@@ -129,7 +130,9 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     from paper_1807_10633_gb300 import vmc
 
     dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)               # every library call of the step runs here
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    torch.cuda.set_stream(stream)
     eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=0, stream=stream)
     W, N2, M = eng.W, 2 * sys_.M, sys_.M
     n_singles, n_same, n_opp = vmc.vmc_lists_info(eng.lists)
@@ -175,6 +178,32 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
             stream.synchronize()                 # the host needs the result before its next step
             p_host.copy_(out_host[:np_])
 
+    graph = None
+    graph_launches = 0
+    if not args.no_graph:
+        l0 = vmc.vmc_launch_count(eng.ctx)
+        step(timed=False, e2e=False, it=0)        # every workspace exists before capture
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        l1 = vmc.vmc_launch_count(eng.ctx)
+        with torch.cuda.graph(graph, stream=stream):
+            step(timed=False, e2e=False, it=0)
+        graph_launches = vmc.vmc_launch_count(eng.ctx) - l1      # kernels in one captured step
+        del l0
+
+    def run_step(timed: bool, e2e: bool, it: int):
+        if graph is None or timed:
+            step(timed=timed, e2e=e2e, it=it)
+            return
+        if e2e:
+            eng.p.copy_(p_host, non_blocking=True)
+        graph.replay()
+        if e2e:
+            out_host[:np_].copy_(eng.p, non_blocking=True)
+            out_host[np_:].copy_(sums, non_blocking=True)
+            stream.synchronize()
+            p_host.copy_(out_host[:np_])
+
     def timed_loop(e2e: bool, it0: int):
         torch.cuda.synchronize()
         if world > 1:
@@ -185,7 +214,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
         launches0 = vmc.vmc_launch_count(eng.ctx)
         t0.record(stream)
         for it in range(args.steps):
-            step(timed=not e2e, e2e=e2e, it=it0 + it)
+            run_step(timed=False, e2e=e2e, it=it0 + it)
         t1.record(stream)
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1)
@@ -195,15 +224,24 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             dist.barrier()
             ms = float(tt.item())
-        return ms, vmc.vmc_launch_count(eng.ctx) - launches0
+        launches = vmc.vmc_launch_count(eng.ctx) - launches0
+        if graph is not None:
+            launches = graph_launches * args.steps
+        return ms, launches
 
     for it in range(args.warmup):
-        step(timed=False, e2e=False, it=it)
+        run_step(timed=False, e2e=False, it=it)
     vmc.vmc_sync(eng.ctx)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
     ms, launches = timed_loop(e2e=False, it0=1000)
     clk = clocks.stop()
+    vmc.vmc_sync(eng.ctx)
+    # local-energy launch time: CUDA events around each launch of one eager step
+    torch.cuda.synchronize()
+    for it in range(2):
+        step(timed=True, e2e=False, it=3000 + it)
+    torch.cuda.synchronize()
     vmc.vmc_sync(eng.ctx)
     eloc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_pairs)
     ms_e2e, _ = timed_loop(e2e=True, it0=2000)
@@ -229,8 +267,10 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
                eloc_gbs=achieved, launches=launches, clocks=clk, energy=energy,
                lists=dict(singles=n_singles, same=n_same, opposite=n_opp), n_params=np_,
                h2d=np_ * 8, d2h=(np_ + 2) * 8)
+    del graph
     eng.close()
     del eng
+    torch.cuda.set_stream(torch.cuda.default_stream(dev))
     torch.cuda.empty_cache()
     return res
 
@@ -272,7 +312,8 @@ def main():
     config = {"workload": f"{args.system} chain STO-3G 1.8 bohr Loewdin, eps={args.eps:g}, "
                           f"{args.walkers} walkers/GPU, {args.sweeps} CTMC sweeps per optimisation step",
               "walkers_per_gpu": args.walkers, "sweeps_per_step": args.sweeps, "eps": args.eps,
-              "l2": "inputs larger than L2 (walker state > 1 GB)"}
+              "l2": "inputs larger than L2 (walker state > 1 GB)",
+              "launch": "eager" if args.no_graph else "one CUDA graph per optimisation step"}
 
     sys_ = load_system(args.system)
     prm = S.make_params(sys_, seed=args.seed)

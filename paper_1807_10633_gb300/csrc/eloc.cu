@@ -100,13 +100,13 @@ struct View {
     __device__ const real *Grow(int s, int slot) const {
         return s ? Gb + (size_t)slot * ldb : Ga + (size_t)slot * lda;
     }
-    const real *E;         // [2M] exp(S) (nullptr: compute from S on the fly)
-    const real *Einv;      // [2M] 1/exp(S) (with E)
+    const real *E;         // [2M] exp(S_p) for virtual p, 1/exp(S_p) for occupied p (nullptr: compute
+                           // from S on the fly)
     const real *S;         // walker S in global (used when E == nullptr)
     const double *F;       // walker F [2][ns]
     Geo geo;
-    __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }
-    __device__ real Eiv(int p) const { return E ? Einv[p] : rrcp(rexp(S[p])); }
+    __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }              // p virtual
+    __device__ real Eiv(int p) const { return E ? E[p] : rrcp(rexp(S[p])); }       // p occupied
     __device__ bool occ(int p) const { return !(pos[p] & 0x8000); }
 };
 
@@ -263,8 +263,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
     real *sGa = (real *)smraw;
     real *sGb = sGa + (size_t)geo.nv_a * lda;
     real *sE = sGb + (size_t)geo.nv_b * ldb;
-    real *sEi = sE + 2 * M;
-    double *eg = (double *)(((uintptr_t)(sEi + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
+    double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
     uint16_t *pos = (uint16_t *)(eg + n_groups);
     __shared__ u128 red_q[VMC_WARPS];
     __shared__ int next_group;
@@ -284,20 +283,20 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
             }
         }
         const real *Sw = (const real *)A.S + (size_t)w * 2 * M;
-        for (int p = tid; p < 2 * M; p += nt) {
-            const real e = rexp(Sw[p]);
-            sE[p] = e;
-            sEi[p] = rrcp(e);
-        }
         const uint16_t *pw = A.pos + (size_t)w * 2 * M;
-        for (int p = tid; p < 2 * M; p += nt) pos[p] = pw[p];
+        for (int p = tid; p < 2 * M; p += nt) {
+            const uint16_t ps = pw[p];
+            const real e = rexp(Sw[p]);
+            sE[p] = (ps & 0x8000) ? e : rrcp(e);
+            pos[p] = ps;
+        }
         if (tid == 0) next_group = VMC_WARPS;
     }
     __syncthreads();
 
     View<real> V;
     V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
-    V.E = sE; V.Einv = sEi; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+    V.E = sE; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
     typedef typename AccT<real>::type acc_t;
     u128 q_tot = 0;
     unsigned flag = 0;
@@ -402,7 +401,7 @@ k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_
         const u128 Tl = T - before;   // threshold inside the group
         View<real> V;
         V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
-        V.E = nullptr; V.Einv = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+        V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, gsel, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -626,7 +625,7 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    const size_t smem = esz * (gpad + 4 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
+    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e;
