@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven batched workload")
+    ap.add_argument("--batch-walkers", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -275,6 +277,70 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     return res
 
 
+BATCH_SYSTEMS = [("hubbard4x4", 0.0), ("hubbard6x6", 0.0), ("hubbard8x8", 0.0), ("hubbard10x10", 0.0),
+                 ("H40", 1e-6), ("H60", 1e-6), ("H100", 1e-6)]
+
+
+def run_batch(args):
+    """Uneven batch: Hubbard L x L (U/t = 4, half filling) and H chains, one launch per sweep step."""
+    import torch
+    from paper_1807_10633_gb300 import vmc
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    torch.cuda.set_stream(stream)
+    engines = []
+    for name, eps in BATCH_SYSTEMS:
+        sys_ = load_system(name)
+        prm = S.make_params(sys_, seed=args.seed)
+        occ = S.init_occupations(sys_, prm, args.batch_walkers, seed=args.seed + 1)
+        engines.append(vmc.Engine(sys_, prm, occ, eps=eps, precision=vmc.VMC_MIXED, device=0, stream=stream))
+    b = vmc.Batch(engines)
+    threads = b.autotune()
+    f64 = dict(dtype=torch.float64, device=dev)
+    acc = []
+    for e in engines:
+        AO, AEO = torch.zeros(e.n_params, **f64), torch.zeros(e.n_params, **f64)
+        acc.append((e.split(AO), e.split(AEO), torch.zeros(2, **f64)))
+
+    def sweep():
+        b.local_energy()
+        for e, (ao, aeo, sm) in zip(engines, acc):
+            vmc.vmc_accumulate_gradient(e.ctx, e.walkers.struct(), e.t_res, e.e_loc, ao, aeo, sm)
+        b.ctmc_step(args.seed)
+
+    for _ in range(max(3, args.warmup)):
+        sweep()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        sweep()
+    g.replay()
+    stream.synchronize()
+    n_sweeps = 8 * max(1, args.steps)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(n_sweeps):
+        g.replay()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / n_sweeps
+    for e in engines:
+        e.sync()
+    res = {"systems": [n for n, _ in BATCH_SYSTEMS], "walkers_per_system": args.batch_walkers,
+           "value": b.W / (ms * 1e-3), "unit": "walker-evals/s", "ms_per_sweep": ms,
+           "sweep": "batched local energy + per-system gradient accumulation + batched CTMC, one CUDA graph",
+           "autotuned_threads_per_walker_cta": threads, "dtype": "f32"}
+    del g
+    for e in engines:
+        e.close()
+    torch.cuda.set_stream(torch.cuda.default_stream(dev))
+    torch.cuda.empty_cache()
+    return res
+
+
 def singles_counts(sys_, eps):
     """Length of every spatial singles list at eps (used for the byte count only)."""
     e = sys_.eri
@@ -370,6 +436,8 @@ def main():
                                  "e2e_value": r["e2e_value"] * scale, "energy_per_electron": r["energy"] / sys_.n_elec}
     if "mixed" in results and "fp64" in results:
         line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
+    if not args.no_batch:
+        line["batched_uneven"] = run_batch(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = args.cpu_sample or max(1, min(os.cpu_count() or 1, 16))
         line["cpu_baseline"] = cpu_baseline(args, sys_, prm, occ, sample)

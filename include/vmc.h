@@ -190,6 +190,38 @@ vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *lists, const vmc_params 
                          vmc_walkers *walkers, uint64_t seed, uint64_t *d_move_code);
 
 /*
+ * Batched launches over several systems of uneven size (for example Hubbard lattices and
+ * hydrogen chains together).  Each item names one system's lists, parameters and walkers with
+ * its own output arrays (d_e_loc, d_t_res: double [W]; d_move_code: uint64 [W]); all items must
+ * use the same precision.  vmc_local_energy_batch computes every walker's local energy in one
+ * launch whose CTAs stay resident and take walkers from a queue, most expensive systems first;
+ * vmc_ctmc_step_batch then moves every walker (selection and update, one launch each).  Results
+ * are identical to the per-system calls (walker index and seed as in vmc_ctmc_step).  The first
+ * call with a new set of items uploads a small descriptor table (not capturable); later calls with
+ * the same items are.  vmc_ctmc_step_batch must follow vmc_local_energy_batch on the same items.
+ */
+typedef struct {
+    const vmc_lists *lists;
+    const vmc_params *params;
+    vmc_walkers *walkers;
+    double eps_run;
+    double *d_e_loc;
+    double *d_t_res;
+    uint64_t *d_move_code;
+} vmc_batch_item;
+
+vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n_items, const vmc_batch_item *items);
+vmc_status vmc_ctmc_step_batch(vmc_ctx *ctx, int n_items, const vmc_batch_item *items, uint64_t seed);
+
+/*
+ * Autotuner for the local-energy launch: times 128, 256 and 512 threads per walker CTA on the
+ * given items (two launches each, CUDA events on the context's stream), keeps the fastest for
+ * later vmc_local_energy / vmc_local_energy_batch calls on this context and returns it.
+ */
+vmc_status vmc_autotune_local_energy(vmc_ctx *ctx, int n_items, const vmc_batch_item *items,
+                                     int *threads_out);
+
+/*
  * Vector-Jacobian product of ln psi (Sec. III.B gradient ratios) for weights w [W] (device):
  *   d_dJ[p][q]  += sum_w w_w n_p n_q   (p < q),   d_dJ[p][p] += sum_w w_w n_p   (upper triangle)
  *   d_dC_s[k][x] += sum_w w_w (C^s_occ)^-1[x][col(k)]   for occupied k of spin s

@@ -97,6 +97,8 @@ vmc_status vmc_destroy(vmc_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->rates) cudaFree(ctx->rates);
+    if (ctx->batch_desc) cudaFree(ctx->batch_desc);
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
     delete ctx;
     return VMC_OK;
 }
@@ -192,6 +194,55 @@ vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, 
     st = launch_ctmc_step(ctx, L, P, Wk, seed, (const u128 *)ctx->rates, ctx->rates_groups, move_code);
     ctx->rates_valid = 0;
     return st;
+}
+
+vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items) {
+    if (!ctx) return VMC_ERR_ARG;
+    for (int k = 0; items && k < n; ++k) {
+        vmc_status st = check_walkers(ctx, items[k].walkers, items[k].lists);
+        if (st) return st;
+    }
+    ctx->rates_valid = 0;
+    return launch_local_energy_batch(ctx, n, items);
+}
+
+vmc_status vmc_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed) {
+    if (!ctx) return VMC_ERR_ARG;
+    for (int k = 0; items && k < n; ++k) {
+        vmc_status st = check_walkers(ctx, items[k].walkers, items[k].lists);
+        if (st) return st;
+    }
+    return launch_ctmc_step_batch(ctx, n, items, seed);
+}
+
+vmc_status vmc_autotune_local_energy(vmc_ctx *ctx, int n, const vmc_batch_item *items, int *threads_out) {
+    if (!ctx) return VMC_ERR_ARG;
+    const int cand[3] = {128, 256, 512};
+    float best = 1e30f;
+    int pick = ctx->eloc_threads;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return set_err(ctx, VMC_ERR_CUDA, "autotune events");
+    for (int c = 0; c < 3; ++c) {
+        ctx->eloc_threads = cand[c];
+        vmc_status st = vmc_local_energy_batch(ctx, n, items);       // warm-up
+        if (st) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
+        cudaEventRecord(a, ctx->stream);
+        st = vmc_local_energy_batch(ctx, n, items);
+        cudaEventRecord(b, ctx->stream);
+        if (st) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_check(ctx, e, "autotune"); }
+        if (ms < best) { best = ms; pick = cand[c]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->eloc_threads = pick;
+    ctx->rates_batch.clear();
+    if (threads_out) *threads_out = pick;
+    return VMC_OK;
 }
 
 vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ, double *dCa,

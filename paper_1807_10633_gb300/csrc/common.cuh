@@ -34,6 +34,13 @@ struct vmc_ctx {
     int rates_valid = 0;
     int rates_groups = 0;
     uint64_t launches = 0;
+    // batched launches: device descriptor table (re-uploaded only when the batch changes)
+    void *batch_desc = nullptr;
+    size_t batch_desc_bytes = 0;
+    std::string batch_host;
+    int *d_queue = nullptr;
+    std::string rates_batch;       // walker tables the batched rate store belongs to
+    int eloc_threads = 256;        // threads per local-energy CTA (set by the autotuner)
 };
 
 // Plain-pointer view of the device lists, passed to kernels by value.
@@ -184,6 +191,8 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
 vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P,
                             vmc_walkers *Wk, uint64_t seed, const u128 *rates, int n_groups,
                             uint64_t *move_code);
+vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items);
+vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ,
                        double *dCa, double *dCb);
 vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,

@@ -15,6 +15,10 @@
 // so the two kernels compute bit-identical rates.
 #include <math.h>
 
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -61,6 +65,16 @@ struct WalkerArgs {
     void *G, *AinvT, *S;
     double *F, *e_diag;
     uint64_t *rng;
+};
+
+struct SysDesc {
+    ListsView L;
+    WalkerArgs A;
+    const double *J;
+    double *e_loc, *t_res;
+    u128 *rates;
+    uint64_t *move_code;
+    int w_begin;
 };
 
 struct Geo {
@@ -251,21 +265,21 @@ __device__ __forceinline__ double warp_sum_acc(float v) {
     return (double)v;
 }
 
+// Local energy of walker w by the whole CTA (any number of warps).  smraw: dynamic shared memory.
 template <typename real>
-__global__ void __launch_bounds__(VMC_THREADS)
-k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
-               u128 *__restrict__ rates, unsigned *status) {
+__device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs &A, const int w,
+                                            double *__restrict__ e_loc, double *__restrict__ t_res,
+                                            u128 *__restrict__ rates, unsigned *status, unsigned char *smraw) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
-    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarp = nt >> 5;
     const int M = geo.M, n_groups = L.n_groups;
     const int lda = geo.na + 1, ldb = geo.nb + 1;    // padded rows: no bank conflicts on columns
-    extern __shared__ __align__(16) unsigned char smraw[];
     real *sGa = (real *)smraw;
     real *sGb = sGa + (size_t)geo.nv_a * lda;
     real *sE = sGb + (size_t)geo.nv_b * ldb;
     double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
     uint16_t *pos = (uint16_t *)(eg + n_groups);
-    __shared__ u128 red_q[VMC_WARPS];
+    __shared__ u128 red_q[32];
     __shared__ int next_group;
 
     // ---- prologue: stage G into padded rows, exp(S), orbital map
@@ -290,7 +304,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
             sE[p] = (ps & 0x8000) ? e : rrcp(e);
             pos[p] = ps;
         }
-        if (tid == 0) next_group = VMC_WARPS;
+        if (tid == 0) next_group = nwarp;
     }
     __syncthreads();
 
@@ -343,7 +357,7 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
         s = warp_sum_f64(s);
         if (lane == 0) {
             u128 Q = 0;
-            for (int k = 0; k < VMC_WARPS; ++k) Q += red_q[k];
+            for (int k = 0; k < nwarp; ++k) Q += red_q[k];
             e_loc[w] = A.e_diag[w] + s;
             if (Q == 0) {
                 t_res[w] = 0.0;
@@ -354,6 +368,35 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
             }
         }
     }
+    __syncthreads();   // shared memory may be reused for the next walker
+}
+
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
+               u128 *__restrict__ rates, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    eloc_walker<real>(L, A, blockIdx.x, e_loc, t_res, rates, status, smraw);
+}
+
+// Batched launch over several systems (uneven sizes).  CTAs stay resident and take walkers from
+// a global queue; the descriptors are ordered by decreasing cost so the long walkers start first.
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_local_energy_batched(const SysDesc *__restrict__ sys, int n_sys, int total, int *queue, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_item;
+        __syncthreads();
+        if (t >= total) break;
+        int k = 0;
+        while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
+        const SysDesc &d = sys[k];
+        eloc_walker<real>(d.L, d.A, t - d.w_begin, d.e_loc, d.t_res, d.rates, status, smraw);
+    }
 }
 
 // ---------------------------------------------------------------------------------- CTMC
@@ -361,13 +404,11 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
 // group whose prefix crosses T and re-walks only that group with the same entry code as the
 // local-energy kernel.  Writes the move code (0 = no move) and advances the walker's counter.
 template <typename real>
-__global__ void __launch_bounds__(VMC_THREADS)
-k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_t seed,
-              uint64_t *__restrict__ move_code, unsigned *status) {
+__device__ __forceinline__ void select_walker(const ListsView &L, const WalkerArgs &A, const int w,
+                                              const u128 *__restrict__ rates, uint64_t seed,
+                                              uint64_t *__restrict__ move_code, unsigned *status) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= A.W) return;
     const int M = geo.M, N2 = 2 * M, n_groups = L.n_groups;
     const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
     const real *Sw = (const real *)A.S + (size_t)w * N2;
@@ -446,22 +487,42 @@ k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_
     }
 }
 
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_t seed,
+              uint64_t *__restrict__ move_code, unsigned *status) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= A.W) return;
+    select_walker<real>(L, A, w, rates, seed, move_code, status);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_ctmc_select_batched(const SysDesc *__restrict__ sys, int n_sys, int total, uint64_t seed, unsigned *status) {
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= total) return;
+    int k = 0;
+    while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
+    const SysDesc &d = sys[k];
+    select_walker<real>(d.L, d.A, t - d.w_begin, d.rates, seed, d.move_code, status);
+}
+
 // Move update: one CTA per walker (Sec. III.B): diagonal energy, Jastrow sums, Fock sums, then the
 // rank-1 (singles, opposite-spin doubles) or rank-2 Woodbury (same-spin doubles) update of G and
 // AinvT, and the occupation lists, bits and orbital map.
 template <typename real>
-__global__ void __launch_bounds__(VMC_THREADS)
-k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint64_t *__restrict__ move_code) {
+__device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArgs &A, const double *__restrict__ J,
+                                             const int w, const uint64_t *__restrict__ move_code,
+                                             unsigned char *smraw) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
-    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarp = nt >> 5;
     const uint64_t code = move_code[w];
     if (code == 0) return;
     const int M = geo.M, ne = geo.ne, N2 = 2 * M;
-    extern __shared__ __align__(16) unsigned char smraw[];
     uint16_t *pos = (uint16_t *)smraw;
     real *vec = (real *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15);
     // vec holds: ua[nmax], ub[nmax], gci[M], gcj[M], arow_i[nmax], arow_j[nmax]
-    __shared__ double red[VMC_WARPS];
+    __shared__ double red[32];
     real *Gw = (real *)A.G + (size_t)w * geo.g_stride;
     real *Aw = (real *)A.AinvT + (size_t)w * geo.a_stride;
     real *Sw = (real *)A.S + (size_t)w * N2;
@@ -494,7 +555,7 @@ k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint
         if (tid == 0) {
             double dE = L.hd[Ao % M] - L.hd[I % M];
             if (kind == 2) dE += L.hd[Bo % M] - L.hd[Jo % M] + D(Bo, Ao) - D(Jo, Ao);
-            for (int k = 0; k < VMC_WARPS; ++k) dE += red[k];
+            for (int k = 0; k < nwarp; ++k) dE += red[k];
             A.e_diag[w] += dE;
         }
     }
@@ -606,6 +667,25 @@ k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint
     }
 }
 
+
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint64_t *__restrict__ move_code) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    apply_walker<real>(L, A, J, blockIdx.x, move_code, smraw);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(512)
+k_ctmc_apply_batched(const SysDesc *__restrict__ sys, int n_sys) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int t = blockIdx.x;
+    int k = 0;
+    while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
+    const SysDesc &d = sys[k];
+    apply_walker<real>(d.L, d.A, d.J, t - d.w_begin, d.move_code, smraw);
+}
+
 }  // namespace
 
 static WalkerArgs make_args(vmc_walkers *Wk) {
@@ -632,13 +712,13 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     if (Wk->precision == VMC_FP64) {
         e = cudaFuncSetAttribute(k_local_energy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_local_energy<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                              ctx->d_status);
+            k_local_energy<double><<<Wk->W, ctx->eloc_threads, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
+                                                                                    ctx->d_status);
     } else {
         e = cudaFuncSetAttribute(k_local_energy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            k_local_energy<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                             ctx->d_status);
+            k_local_energy<float><<<Wk->W, ctx->eloc_threads, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
+                                                                                   ctx->d_status);
     }
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -671,4 +751,160 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
     ctx->launches += 2;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_ctmc_select/k_ctmc_apply");
+}
+
+// ---------------------------------------------------------------------------------- batches
+static size_t eloc_smem_bytes(const vmc_lists *L, const vmc_walkers *Wk) {
+    const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
+    const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
+    const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
+    return esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
+}
+
+static size_t apply_smem_bytes(const vmc_walkers *Wk) {
+    const int M = Wk->M, nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
+    const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
+    return 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
+}
+
+// Builds (and uploads when changed) the descriptor table of a batch, most expensive systems
+// first.  Also sizes the shared rate store.  Outputs: total walkers, max shared memory.
+static vmc_status prepare_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, int *total,
+                                size_t *smem_eloc, size_t *smem_apply, int *precision) {
+    extern vmc_status lists_set_eps(vmc_ctx *, vmc_lists *, double);
+    if (n < 1 || n > 64 || !items) return set_err(ctx, VMC_ERR_ARG, "1 to 64 batch items");
+    std::vector<int> order(n);
+    std::vector<double> cost(n);
+    for (int k = 0; k < n; ++k) {
+        const vmc_batch_item &it = items[k];
+        if (!it.lists || !it.params || !it.walkers || !it.d_e_loc || !it.d_t_res || !it.d_move_code)
+            return set_err(ctx, VMC_ERR_ARG, "null batch item field");
+        if (it.walkers->precision != items[0].walkers->precision)
+            return set_err(ctx, VMC_ERR_ARG, "batch items must share the precision");
+        if (it.walkers->M != it.lists->M) return set_err(ctx, VMC_ERR_ARG, "lists and walkers disagree on M");
+        if (!(it.eps_run >= it.lists->eps_build)) return set_err(ctx, VMC_ERR_ARG, "eps_run below the build eps");
+        vmc_status st = lists_set_eps(ctx, const_cast<vmc_lists *>(it.lists), it.eps_run);
+        if (st) return st;
+        order[k] = k;
+        const vmc_lists *L = it.lists;
+        cost[k] = (double)(L->ns + 2 * L->nds + L->ndo) * (it.walkers->n_alpha + it.walkers->n_beta) / (2.0 * L->M) +
+                  (double)walker_stride_G(it.walkers->M, it.walkers->n_alpha, it.walkers->n_beta);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    size_t rates_total = 0;
+    std::vector<size_t> rate_off(n);
+    int tot = 0;
+    size_t se = 0, sa = 0;
+    for (int k = 0; k < n; ++k) {
+        const vmc_batch_item &it = items[order[k]];
+        rate_off[k] = rates_total;
+        rates_total += (size_t)it.walkers->W * it.lists->view.n_groups;
+        tot += it.walkers->W;
+        se = std::max(se, eloc_smem_bytes(it.lists, it.walkers));
+        sa = std::max(sa, apply_smem_bytes(it.walkers));
+    }
+    if (rates_total * sizeof(u128) > ctx->rates_bytes) {
+        if (ctx->rates) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->rates); ctx->rates = nullptr; }
+        cudaError_t e = cudaMalloc(&ctx->rates, rates_total * sizeof(u128));
+        if (e != cudaSuccess) { ctx->rates_bytes = 0; return cuda_check(ctx, e, "batched rate store"); }
+        ctx->rates_bytes = rates_total * sizeof(u128);
+    }
+    std::string tab(sizeof(SysDesc) * n, '\0');
+    SysDesc *d = (SysDesc *)&tab[0];
+    int wb = 0;
+    for (int k = 0; k < n; ++k) {
+        const vmc_batch_item &it = items[order[k]];
+        d[k].L = it.lists->view;
+        d[k].A = make_args(it.walkers);
+        d[k].J = it.params->J;
+        d[k].e_loc = it.d_e_loc;
+        d[k].t_res = it.d_t_res;
+        d[k].rates = (u128 *)ctx->rates + rate_off[k];
+        d[k].move_code = it.d_move_code;
+        d[k].w_begin = wb;
+        wb += it.walkers->W;
+    }
+    if (tab != ctx->batch_host) {
+        if (tab.size() > ctx->batch_desc_bytes) {
+            if (ctx->batch_desc) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->batch_desc); }
+            cudaError_t e = cudaMalloc(&ctx->batch_desc, tab.size());
+            if (e != cudaSuccess) { ctx->batch_desc = nullptr; ctx->batch_desc_bytes = 0; return cuda_check(ctx, e, "batch table"); }
+            ctx->batch_desc_bytes = tab.size();
+        }
+        if (!ctx->d_queue) {
+            cudaError_t e = cudaMalloc(&ctx->d_queue, sizeof(int));
+            if (e != cudaSuccess) { ctx->d_queue = nullptr; return cuda_check(ctx, e, "batch queue"); }
+        }
+        cudaError_t e = cudaMemcpyAsync(ctx->batch_desc, tab.data(), tab.size(), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "batch table upload");
+        ctx->batch_host = tab;
+    }
+    *total = tot;
+    *smem_eloc = se;
+    *smem_apply = sa;
+    *precision = items[0].walkers->precision;
+    return VMC_OK;
+}
+
+static std::string batch_signature(int n, const vmc_batch_item *items) {
+    std::string sig;
+    for (int k = 0; k < n; ++k) sig.append((const char *)&items[k].walkers->G, sizeof(void *));
+    return sig;
+}
+
+vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items) {
+    int total = 0, prec = 0;
+    size_t se = 0, sa = 0;
+    vmc_status st = prepare_batch(ctx, n, items, &total, &se, &sa, &prec);
+    if (st) return st;
+    if (se > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
+    cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = ctx->eloc_threads;
+    const SysDesc *tab = (const SysDesc *)ctx->batch_desc;
+    if (prec == VMC_FP64) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_local_energy_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_energy_batched<double>, threads, se);
+        if (e == cudaSuccess)
+            k_local_energy_batched<double><<<std::max(1, per_sm) * nsm, threads, se, ctx->stream>>>(tab, n, total, ctx->d_queue, ctx->d_status);
+    } else {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_local_energy_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_energy_batched<float>, threads, se);
+        if (e == cudaSuccess)
+            k_local_energy_batched<float><<<std::max(1, per_sm) * nsm, threads, se, ctx->stream>>>(tab, n, total, ctx->d_queue, ctx->d_status);
+    }
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "k_local_energy_batched");
+    ctx->rates_batch = batch_signature(n, items);
+    ctx->rates_valid = 0;
+    return VMC_OK;
+}
+
+vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed) {
+    if (ctx->rates_batch.empty() || ctx->rates_batch != batch_signature(n, items))
+        return set_err(ctx, VMC_ERR_ARG, "vmc_local_energy_batch must precede vmc_ctmc_step_batch on the same items");
+    int total = 0, prec = 0;
+    size_t se = 0, sa = 0;
+    vmc_status st = prepare_batch(ctx, n, items, &total, &se, &sa, &prec);
+    if (st) return st;
+    const SysDesc *tab = (const SysDesc *)ctx->batch_desc;
+    const int sel_blocks = (total + 7) / 8;
+    cudaError_t e;
+    if (prec == VMC_FP64) {
+        k_ctmc_select_batched<double><<<sel_blocks, 256, 0, ctx->stream>>>(tab, n, total, seed, ctx->d_status);
+        e = cudaFuncSetAttribute(k_ctmc_apply_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+        if (e == cudaSuccess) k_ctmc_apply_batched<double><<<total, 256, sa, ctx->stream>>>(tab, n);
+    } else {
+        k_ctmc_select_batched<float><<<sel_blocks, 256, 0, ctx->stream>>>(tab, n, total, seed, ctx->d_status);
+        e = cudaFuncSetAttribute(k_ctmc_apply_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+        if (e == cudaSuccess) k_ctmc_apply_batched<float><<<total, 256, sa, ctx->stream>>>(tab, n);
+    }
+    ctx->launches += 2;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    ctx->rates_batch.clear();
+    return cuda_check(ctx, e, "k_ctmc_*_batched");
 }

@@ -274,10 +274,12 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
             }
         for (size_t t = 0; t < MM * MM; ++t)
             if (!ol[t].empty()) band = std::max(band, std::abs((int)(t / M) - (int)(t % M)));
-        // candidates of an alpha row: same-spin q in (p, p+band], opposite q in [p-band, p+band]
+        // candidates of an alpha row: same-spin q in (p, p+band], opposite q in [p-band, p+band];
+        // no row groups at all when every double list is empty (e.g. the Hubbard model)
+        bool any_double = nds > 0 || ndo > 0;
         const int cand = std::min(band, M - 1) + std::min(2 * band + 1, M);
         v.band = band;
-        v.cpr = std::max(1, (cand + 31) / 32);
+        v.cpr = any_double ? std::max(1, (cand + 31) / 32) : 0;
         v.n_groups = (2 * M + 31) / 32 + 2 * M * v.cpr;
     }
     v.s_off = (const uint32_t *)P(i_s_off); v.s_len = (const uint32_t *)P(i_s_len);

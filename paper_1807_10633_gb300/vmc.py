@@ -38,6 +38,12 @@ class vmc_params(ct.Structure):
     _fields_ = [("J", ct.c_void_p), ("C_alpha", ct.c_void_p), ("C_beta", ct.c_void_p)]
 
 
+class vmc_batch_item(ct.Structure):
+    _fields_ = [("lists", ct.c_void_p), ("params", ct.POINTER(vmc_params)), ("walkers", ct.POINTER(vmc_walkers)),
+                ("eps_run", ct.c_double), ("d_e_loc", ct.c_void_p), ("d_t_res", ct.c_void_p),
+                ("d_move_code", ct.c_void_p)]
+
+
 _lib = None
 
 
@@ -71,6 +77,9 @@ def lib() -> ct.CDLL:
             "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
             "vmc_grad_logpsi_noalloc": ([ct.POINTER(vmc_walkers), P, P, P, P, P], I),
+            "vmc_local_energy_batch": ([P, I, ct.POINTER(vmc_batch_item)], I),
+            "vmc_ctmc_step_batch": ([P, I, ct.POINTER(vmc_batch_item), U64], I),
+            "vmc_autotune_local_energy": ([P, I, ct.POINTER(vmc_batch_item), ct.POINTER(I)], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -200,6 +209,20 @@ def vmc_grad_logpsi_noalloc(walkers, w, dJ, dCa, dCb, stream=None):
     st = lib().vmc_grad_logpsi_noalloc(ct.byref(walkers), _ptr(w), _ptr(dJ), _ptr(dCa), _ptr(dCb), s)
     if st != 0:
         raise VmcError(st, "vmc_grad_logpsi_noalloc")
+
+
+def vmc_local_energy_batch(ctx, items):
+    _check(ctx, lib().vmc_local_energy_batch(ctx, len(items), items))
+
+
+def vmc_ctmc_step_batch(ctx, items, seed):
+    _check(ctx, lib().vmc_ctmc_step_batch(ctx, len(items), items, int(seed)))
+
+
+def vmc_autotune_local_energy(ctx, items) -> int:
+    out = ct.c_int()
+    _check(ctx, lib().vmc_autotune_local_energy(ctx, len(items), items, ct.byref(out)))
+    return out.value
 
 
 def vmc_launch_count(ctx) -> int:
@@ -350,6 +373,35 @@ class Engine:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several engines (systems of uneven size, same precision) driven by batched launches."""
+
+    def __init__(self, engines):
+        self.engines = list(engines)
+        self.ctx = self.engines[0].ctx
+        self._keep = []
+        self.items = (vmc_batch_item * len(self.engines))()
+        for k, e in enumerate(self.engines):
+            prm = e.params
+            ws = e.walkers.struct()
+            self._keep += [prm, ws]
+            self.items[k] = vmc_batch_item(e.lists, ct.pointer(prm), ct.pointer(ws), e.eps, _ptr(e.e_loc),
+                                           _ptr(e.t_res), _ptr(e.moves))
+
+    @property
+    def W(self) -> int:
+        return sum(e.W for e in self.engines)
+
+    def local_energy(self):
+        vmc_local_energy_batch(self.ctx, self.items)
+
+    def ctmc_step(self, seed: int):
+        vmc_ctmc_step_batch(self.ctx, self.items, seed)
+
+    def autotune(self) -> int:
+        return vmc_autotune_local_energy(self.ctx, self.items)
 
 
 class LogPsi(torch.autograd.Function):
