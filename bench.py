@@ -138,6 +138,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=0, stream=stream)
     W, N2, M = eng.W, 2 * sys_.M, sys_.M
     n_singles, n_same, n_opp = vmc.vmc_lists_info(eng.lists)
+    eloc_threads = vmc.Batch([eng]).autotune()    # threads per walker CTA for the local energy
     np_ = eng.n_params
     f64 = dict(dtype=torch.float64, device=dev)
     AO = torch.zeros(np_, **f64)
@@ -267,7 +268,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     res = dict(value=evals / (ms * 1e-3), ms_per_step=ms / args.steps, ms_e2e=ms_e2e / args.steps,
                e2e_value=evals / (ms_e2e * 1e-3), eloc_ms=eloc_ms, eloc_bytes=bytes_launch,
                eloc_gbs=achieved, launches=launches, clocks=clk, energy=energy,
-               lists=dict(singles=n_singles, same=n_same, opposite=n_opp), n_params=np_,
+               lists=dict(singles=n_singles, same=n_same, opposite=n_opp), n_params=np_, eloc_threads=eloc_threads,
                h2d=np_ * 8, d2h=(np_ + 2) * 8)
     del graph
     eng.close()
@@ -422,6 +423,7 @@ def main():
             "e2e": {"value": head["e2e_value"] * scale, "unit": UNIT, "h2d_bytes_per_step": head["h2d"],
                     "d2h_bytes_per_step": head["d2h"]},
             "gpu_launches": head["launches"],
+            "eloc_threads_per_walker_cta": head["eloc_threads"],
             "roofline": {"kernel": "k_local_energy", "bound": "hbm", "achieved": head["eloc_gbs"],
                          "peak": peak, "unit": "GB/s", "frac": head["eloc_gbs"] / peak,
                          "peak_source": peak_kind, "traffic": None,
