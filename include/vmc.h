@@ -281,6 +281,13 @@ vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const d
 vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w, double *d_dJ,
                                    double *d_dC_alpha, double *d_dC_beta, void *cuda_stream);
 
+/* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the mixed-form refresh forms
+   G = C C_occ^-1 with tcgen05 TF32 MMAs and a split-precision correction (0: FP32 CUDA cores).
+   VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256 or 512). */
+#define VMC_OPT_G_TENSOR_CORES 1
+#define VMC_OPT_ELOC_THREADS 2
+vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value);
+
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */
 uint64_t vmc_launch_count(const vmc_ctx *ctx);
 

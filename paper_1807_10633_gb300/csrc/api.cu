@@ -109,6 +109,20 @@ vmc_status vmc_set_stream(vmc_ctx *ctx, void *stream) {
     return VMC_OK;
 }
 
+vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value) {
+    if (!ctx) return VMC_ERR_ARG;
+    if (option == VMC_OPT_G_TENSOR_CORES) {
+        ctx->g_tensor_cores = value ? 1 : 0;
+        return VMC_OK;
+    }
+    if (option == VMC_OPT_ELOC_THREADS) {
+        if (value != 128 && value != 256 && value != 512) return set_err(ctx, VMC_ERR_ARG, "128, 256 or 512 threads");
+        ctx->eloc_threads = value;
+        return VMC_OK;
+    }
+    return set_err(ctx, VMC_ERR_ARG, "unknown option");
+}
+
 const char *vmc_last_error(const vmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 uint64_t vmc_launch_count(const vmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
@@ -125,6 +139,7 @@ vmc_status vmc_sync(vmc_ctx *ctx) {
     if (st & VMC_DEV_OVERFLOW) return set_err(ctx, VMC_ERR_OVERFLOW, "CTMC rate reached 2^43");
     if (st & VMC_DEV_NOMOVE) return set_err(ctx, VMC_ERR_NOMOVE, "walker without an allowed move");
     if (st & VMC_DEV_INCONSISTENT) return set_err(ctx, VMC_ERR_ARG, "rate store inconsistent with walkers");
+    if (st & VMC_DEV_TIMEOUT) return set_err(ctx, VMC_ERR_TIMEOUT, "a bounded device wait gave up");
     return VMC_OK;
 }
 

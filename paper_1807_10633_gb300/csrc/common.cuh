@@ -19,6 +19,7 @@ typedef unsigned __int128 u128;
 #define VMC_DEV_OVERFLOW 2u
 #define VMC_DEV_NOMOVE 4u
 #define VMC_DEV_INCONSISTENT 8u
+#define VMC_DEV_TIMEOUT 16u
 
 struct vmc_ctx {
     int device = 0;
@@ -41,6 +42,7 @@ struct vmc_ctx {
     int *d_queue = nullptr;
     std::string rates_batch;       // walker tables the batched rate store belongs to
     int eloc_threads = 256;        // threads per local-energy CTA (set by the autotuner)
+    int g_tensor_cores = 1;        // mixed refresh: G on tcgen05 (1) or CUDA cores (0)
 };
 
 // Plain-pointer view of the device lists, passed to kernels by value.
@@ -193,6 +195,7 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
                             uint64_t *move_code);
 vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items);
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
+vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);
 vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ,
                        double *dCa, double *dCb);
 vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,

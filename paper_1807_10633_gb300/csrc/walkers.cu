@@ -207,7 +207,7 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
                     const float *__restrict__ Cf, uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all,
-                    uint32_t *occ_bits, float *G, float *AinvT, unsigned *status) {
+                    uint32_t *occ_bits, float *G, float *AinvT, unsigned *status, int do_g) {
     const int w = blockIdx.x, sg = blockIdx.y;
     const int n = sg ? nb : na, nv = M - n;
     const int ne = na + nb, nw = (M + 31) / 32;
@@ -348,6 +348,7 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         const int c = t / n, x = t % n;
         AinvT[aofs + t] = Y[c * ld + x];
     }
+    if (!do_g) return;   // G is formed on the tensor cores by k_g_umma
     // G[s][c] = sum_x C[virt[s]][x] AinvT[c][x]: 4 x 4 register tiles (slots x columns)
     const int ts = (nv + 3) / 4, tc = (n + 3) / 4;
     for (int tile = tid; tile < ts * tc; tile += nt) {
@@ -550,11 +551,17 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
         float *Cf = (float *)L->cf;
         k_convert_c<<<(M * (na + nb) + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, P->C_alpha, P->C_beta, Cf);
         ctx->launches += 1;
+        const int nvmax = M - (na < nb ? na : nb);
+        const bool umma = ctx->g_tensor_cores && nmax >= 1 && nmax <= 128 && nvmax <= 128;
         e = cudaFuncSetAttribute(k_init_tables_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         if (e == cudaSuccess)
             k_init_tables_mixed<<<grid, VMC_THREADS, smem_m, ctx->stream>>>(
                 M, na, nb, P->C_alpha, P->C_beta, Cf, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits,
-                (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status);
+                (float *)Wk->G, (float *)Wk->AinvT, ctx->d_status, umma ? 0 : 1);
+        if (e == cudaSuccess && umma) {
+            vmc_status st2 = launch_g_umma(ctx, Wk, Cf);
+            if (st2) return st2;
+        }
     }
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();

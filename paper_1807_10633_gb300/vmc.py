@@ -16,6 +16,7 @@ import torch
 from .build import LIB
 
 VMC_FP64, VMC_MIXED = 0, 1
+VMC_OPT_G_TENSOR_CORES, VMC_OPT_ELOC_THREADS = 1, 2
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SINGULAR", 5: "ERR_TIMEOUT",
            6: "ERR_OVERFLOW", 7: "ERR_NOMOVE"}
 
@@ -76,6 +77,7 @@ def lib() -> ct.CDLL:
             "vmc_energy_gradient": ([P, ct.c_size_t, P, P, P, P], I),
             "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
+            "vmc_set_option": ([P, I, I], I),
             "vmc_grad_logpsi_noalloc": ([ct.POINTER(vmc_walkers), P, P, P, P, P], I),
             "vmc_local_energy_batch": ([P, I, ct.POINTER(vmc_batch_item)], I),
             "vmc_ctmc_step_batch": ([P, I, ct.POINTER(vmc_batch_item), U64], I),
@@ -223,6 +225,10 @@ def vmc_autotune_local_energy(ctx, items) -> int:
     out = ct.c_int()
     _check(ctx, lib().vmc_autotune_local_energy(ctx, len(items), items, ct.byref(out)))
     return out.value
+
+
+def vmc_set_option(ctx, option: int, value: int):
+    _check(ctx, lib().vmc_set_option(ctx, option, value))
 
 
 def vmc_launch_count(ctx) -> int:
