@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven batched workload")
+    ap.add_argument("--g-cuda-cores", action="store_true", help="form G on CUDA cores instead of tcgen05")
     ap.add_argument("--batch-walkers", type=int, default=2048)
     return ap.parse_args()
 
@@ -136,6 +137,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     stream.wait_stream(torch.cuda.current_stream(dev))
     torch.cuda.set_stream(stream)
     eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=0, stream=stream)
+    if args.g_cuda_cores:
+        vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, 0)
     W, N2, M = eng.W, 2 * sys_.M, sys_.M
     n_singles, n_same, n_opp = vmc.vmc_lists_info(eng.lists)
     eloc_threads = vmc.Batch([eng]).autotune()    # threads per walker CTA for the local energy

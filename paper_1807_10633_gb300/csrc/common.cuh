@@ -196,6 +196,7 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
 vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items);
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);
+size_t g_umma_smem(int M, int na, int nb);
 vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ,
                        double *dCa, double *dCb);
 vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,

@@ -1,15 +1,15 @@
 // G = C_v C_occ^-1 on the 5th-generation tensor cores (tcgen05, TF32) with a split-precision
 // correction, for the mixed-form refresh of the walker tables (Sec. III.B, Eq. R).
 //
-// Per (walker, spin) CTA of four warps:
-//   A (M = 128 rows >= n_virt, K = n): rows of C (FP32 copy) for the walker's virtual orbitals;
-//   B (N = n rounded up to 16, K = n):  rows of C_occ^-1 transposed (AinvT[c][x], K-major);
-//   D = A_hi B_hi + A_hi B_lo + A_lo B_hi  (x_hi = x truncated to TF32, x_lo = x - x_hi),
-// accumulated in FP32 in tensor memory, which recovers ~22 bits from TF32 products.  Operands
-// are staged in shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
-// core matrix); one thread issues the MMAs and commits them to an mbarrier whose wait is bounded
-// (on timeout the kernel latches VMC_ERR_TIMEOUT, frees its tensor memory and returns).
+// Products are split: D = A_hi B_hi + A_hi B_lo + A_lo B_hi (x_hi = x truncated to TF32,
+// x_lo = x - x_hi), accumulated in FP32 in tensor memory, which recovers ~22 bits from TF32
+// products.  Operands are staged in shared memory in the no-swizzle K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix); one thread issues the MMAs and commits them to an
+// mbarrier whose waits are bounded (on timeout the kernel latches VMC_ERR_TIMEOUT, frees its
+// tensor memory and returns).
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -49,108 +49,69 @@ __device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
     lo = v - hi;
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_g_umma(int M, int na, int nb, const float *__restrict__ Cf, const uint16_t *__restrict__ virt_list,
+// Bounded wait on an mbarrier phase; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (unsigned spin = 0; spin < kMaxSpin && !done; ++spin)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity));
+    return done != 0;
+}
+
+// Persistent, pipelined G refresh.  Items are (spin, walker) pairs; CTA b takes a contiguous range.
+//   MMA operand A (M = 128 >= n rows): AinvT[c][x] of the item's walker and spin (K-major);
+//   MMA operand B (N = M_orb rounded up to 16): C^sigma[k][x] for every orbital k, staged once
+//   per spin and shared by all items of the CTA;
+//   D[c][k] = sum_x AinvT[c][x] C[k][x] = G_full[k][c]; the epilogue keeps the virtual rows k.
+// A and the tensor-memory accumulator are double buffered: staging item i+1 and draining item i-1
+// overlap the MMAs of item i.  Rows n..127 of the A tile are never written: they read whatever
+// follows in shared memory and only feed output rows that are discarded.
+__global__ void __launch_bounds__(kThreads, 1)
+k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint16_t *__restrict__ pos_all,
          const float *__restrict__ AinvT, float *__restrict__ G, unsigned *status, int lbo_k_major) {
-    const int w = blockIdx.x, sg = blockIdx.y;
-    const int n = sg ? nb : na, nv = M - n;
-    const int ne = na + nb;
-    if (n == 0 || nv == 0) return;
-    const int Kp = (n + 7) & ~7, Np = (n + 15) & ~15, kp4 = Kp >> 2;
+    const int nmax = na > nb ? na : nb;
+    const int Kp = (nmax + 7) & ~7, kp4 = Kp >> 2, Mp = (M + 15) & ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const uint32_t a_bytes = (uint32_t)(kM / 8) * kp4 * 128, b_bytes = (uint32_t)(Np / 8) * kp4 * 128;
-    unsigned char *Ahi = sm, *Alo = Ahi + a_bytes, *Bhi = Alo + a_bytes, *Blo = Bhi + b_bytes;
-    __shared__ __align__(8) uint64_t mbar;
+    const uint32_t a_bytes = (uint32_t)((nmax + 7) / 8) * kp4 * 128, b_bytes = (uint32_t)(Mp / 8) * kp4 * 128;
+    unsigned char *Abuf = sm;                                  // [2 buffers][hi, lo] of a_bytes
+    unsigned char *Bh = sm + 4 * a_bytes, *Bl = Bh + b_bytes;  // C^sigma hi / lo
+    uint16_t *posb = (uint16_t *)(Bl + b_bytes);               // [2][M] orbital map of the item
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int timed_out;
-
-    const float *Cs = Cf + (sg ? (size_t)M * na : 0);
-    const uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
-    const float *At = AinvT + (size_t)w * ((size_t)na * na + (size_t)nb * nb) + (sg ? (size_t)na * na : 0);
-
-    // ---- stage the operands (zero K padding; rows beyond nv / n only feed unused outputs)
-    for (int t = tid; t < kM * Kp; t += kThreads) {
-        const int r = t / Kp, k = t - r * Kp;
-        float v = 0.0f;
-        if (r < nv && k < n) v = Cs[(size_t)vl[r] * n + k];
-        float hi, lo;
-        split_tf32(v, hi, lo);
-        const uint32_t o = core_off(r, k, kp4);
-        *(float *)(Ahi + o) = hi;
-        *(float *)(Alo + o) = lo;
-    }
-    for (int t = tid; t < Np * Kp; t += kThreads) {
-        const int r = t / Kp, k = t - r * Kp;
-        float v = 0.0f;
-        if (r < n && k < n) v = At[(size_t)r * n + k];
-        float hi, lo;
-        split_tf32(v, hi, lo);
-        const uint32_t o = core_off(r, k, kp4);
-        *(float *)(Bhi + o) = hi;
-        *(float *)(Blo + o) = lo;
-    }
+    __shared__ int abort_flag;
+    const size_t gstride = (size_t)(M - na) * na + (size_t)(M - nb) * nb;
+    const size_t astride = (size_t)na * na + (size_t)nb * nb;
+    const int total = 2 * W, per = (total + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * per, t1 = min(total, t0 + per);
+    if (t0 >= t1) return;
     if (tid == 0) {
-        timed_out = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == 0) {   // allocate 128 columns of tensor memory (N <= 128)
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_base)));
+    if (warp == 0) {   // two accumulators of Mp <= 256 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("fence.proxy.async.shared::cta;");   // generic-proxy stores -> tensor-core reads
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
+    uint32_t phase[2] = {0u, 0u};
+    int cur_spin = -1, prev = -1, prev_buf = 0, it = 0;
 
-    // ---- one thread issues the MMAs: K steps of 8, three products each
-    if (tid == 0) {
-        const uint32_t idesc = make_idesc(kM, Np);
-        // no-swizzle K-major: core matrices along K are 128 B apart, row groups kp4 * 128 B apart
-        const uint32_t kstride = 128, rstride = (uint32_t)kp4 * 128;
-        const uint32_t lbo = lbo_k_major ? kstride : rstride, sbo = lbo_k_major ? rstride : kstride;
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-        for (int ks = 0; ks < Kp / 8; ++ks) {
-            const uint32_t koff = (uint32_t)ks * 256;   // two core matrices along K
-            const uint64_t dah = make_desc(ah + koff, lbo, sbo), dal = make_desc(al + koff, lbo, sbo);
-            const uint64_t dbh = make_desc(bh + koff, lbo, sbo), dbl = make_desc(bl + koff, lbo, sbo);
-            const uint32_t acc0 = ks > 0 ? 1u : 0u;
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                         ::"r"(tmem), "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                         ::"r"(tmem), "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                         ::"r"(tmem), "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(smem_u32(&mbar)));
-    }
-    // ---- bounded wait for the MMAs
-    {
-        uint32_t done = 0;
-        unsigned spin = 0;
-        while (!done && spin < kMaxSpin) {
-            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-                         "selp.u32 %0, 1, 0, p;\n\t}"
-                         : "=r"(done) : "r"(smem_u32(&mbar)));
-            ++spin;
-        }
-        if (!done) atomicOr(&timed_out, 1);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (!timed_out) {
-        // ---- read D: warp w owns tensor-memory lanes 32w..32w+31 (= rows), 16 columns at a time
-        const int row = warp * 32 + lane;
-        float *Gw = G + (size_t)w * ((size_t)(M - na) * na + (size_t)(M - nb) * nb) + (sg ? (size_t)(M - na) * na : 0);
-        for (int c0 = 0; c0 < Np; c0 += 16) {
+    // epilogue of item q (accumulator buffer bq): G[w][slot(k)][c] = D[c][k] for virtual k
+    auto epilogue = [&](int q, int bq) {
+        const int s = q >= W, w = q - s * W, n = s ? nb : na;
+        float *Gw = G + (size_t)w * gstride + (s ? (size_t)(M - na) * na : 0);
+        const uint16_t *pq = posb + bq * M;
+        const int c = warp * 32 + lane;
+        for (int k0 = 0; k0 < Mp; k0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + (uint32_t)(bq * 256) + ((uint32_t)(warp * 32) << 16) + (uint32_t)k0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
@@ -158,38 +119,144 @@ k_g_umma(int M, int na, int nb, const float *__restrict__ Cf, const uint16_t *__
                            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < nv) {
+            if (c < n) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < n) Gw[(size_t)row * n + c0 + j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) {
+                    const int k = k0 + j;
+                    if (k < M) {
+                        const uint16_t pk = pq[k];
+                        if (pk & 0x8000) Gw[(size_t)(pk & 0x7FFF) * n + c] = __uint_as_float(r[j]);
+                    }
+                }
             }
         }
-    } else if (tid == 0) {
-        atomicOr(status, VMC_DEV_TIMEOUT);
+    };
+
+    for (int t = t0; t < t1 && !abort_flag; ++t, ++it) {
+        const int s = t >= W, w = t - s * W, n = s ? nb : na;
+        const int buf = it & 1;
+        if (s != cur_spin) {   // (re)stage C^sigma after draining the pipeline
+            if (prev >= 0) {
+                if (!mbar_wait(&mbar[prev_buf], phase[prev_buf])) { if (tid == 0) abort_flag = 1; }
+                phase[prev_buf] ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                __syncthreads();
+                if (abort_flag) break;
+                epilogue(prev, prev_buf);
+                prev = -1;
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+            }
+            const float *Cs = Cf + (s ? (size_t)M * na : 0);
+            for (int e = tid; e < Mp * Kp; e += kThreads) {
+                const int r = e / Kp, k = e - r * Kp;
+                const float v = (r < M && k < n) ? Cs[(size_t)r * n + k] : 0.0f;
+                float hi, lo;
+                split_tf32(v, hi, lo);
+                const uint32_t o = core_off(r, k, kp4);
+                *(float *)(Bh + o) = hi;
+                *(float *)(Bl + o) = lo;
+            }
+            cur_spin = s;
+        }
+        // stage A = AinvT of item t into buffer `buf`, and its orbital map
+        unsigned char *Ah = Abuf + (size_t)(2 * buf) * a_bytes, *Al = Ah + a_bytes;
+        const float *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
+        for (int e = tid; e < n * Kp; e += kThreads) {
+            const int r = e / Kp, k = e - r * Kp;
+            const float v = k < n ? At[(size_t)r * n + k] : 0.0f;
+            float hi, lo;
+            split_tf32(v, hi, lo);
+            const uint32_t o = core_off(r, k, kp4);
+            *(float *)(Ah + o) = hi;
+            *(float *)(Al + o) = lo;
+        }
+        const uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)s * M;
+        for (int k = tid; k < M; k += kThreads) posb[buf * M + k] = pw[k];
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t idesc = make_idesc(kM, Mp);
+            const uint32_t kstride = 128, ra = (uint32_t)kp4 * 128;
+            const uint32_t lbo = lbo_k_major ? kstride : ra, sbo = lbo_k_major ? ra : kstride;
+            const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+            const uint32_t acc = tmem + (uint32_t)(buf * 256);
+            for (int ks = 0; ks < Kp / 8; ++ks) {
+                const uint32_t koff = (uint32_t)ks * 256;
+                const uint64_t dah = make_desc(ah + koff, lbo, sbo), dal = make_desc(al + koff, lbo, sbo);
+                const uint64_t dbh = make_desc(bh + koff, lbo, sbo), dbl = make_desc(bl + koff, lbo, sbo);
+                const uint32_t acc0 = ks > 0 ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(acc), "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(acc), "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(acc), "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&mbar[buf])));
+        }
+        // drain the previous item while these MMAs run
+        if (prev >= 0) {
+            if (!mbar_wait(&mbar[prev_buf], phase[prev_buf])) { if (tid == 0) abort_flag = 1; }
+            phase[prev_buf] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            __syncthreads();
+            if (abort_flag) break;
+            epilogue(prev, prev_buf);
+        }
+        prev = t;
+        prev_buf = buf;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
     }
+    if (prev >= 0 && !abort_flag) {
+        if (!mbar_wait(&mbar[prev_buf], phase[prev_buf])) { if (tid == 0) abort_flag = 1; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (!abort_flag) epilogue(prev, prev_buf);
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(status, VMC_DEV_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
     }
 }
 
 }  // namespace
 
-// Returns VMC_ERR_ARG (nothing launched) when the shapes are outside the kernel's range.
+// Shared memory of the persistent G kernel, or 0 when the shapes are outside its range.
+size_t g_umma_smem(int M, int na, int nb) {
+    const int nmax = na > nb ? na : nb;
+    if (nmax < 1 || nmax > 128 || M > 256) return 0;
+    const int Kp = (nmax + 7) & ~7, Mp = (M + 15) & ~15;
+    const size_t a = (size_t)((nmax + 7) / 8) * (Kp / 4) * 128, b = (size_t)(Mp / 8) * (Kp / 4) * 128;
+    // the MMA reads 128 rows (16 row groups) from the start of every A buffer, the last one included
+    const size_t tile = (size_t)16 * (Kp / 4) * 128;
+    const size_t bytes = std::max(4 * a + 2 * b + 2 * 2 * (size_t)M, 3 * a + tile) + 1024;
+    return bytes <= 220 * 1024 ? bytes : 0;
+}
+
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf) {
     const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
-    const int nmax = na > nb ? na : nb;
-    const int nvmax = M - (na < nb ? na : nb);
-    if (nmax > 128 || nvmax > kM || nmax < 1) return VMC_ERR_ARG;
-    const int Kp = (nmax + 7) & ~7, Np = (nmax + 15) & ~15;
-    const size_t smem = (size_t)2 * (kM / 8) * (Kp / 4) * 128 + (size_t)2 * (Np / 8) * (Kp / 4) * 128 + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_g_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = g_umma_smem(M, na, nb);
+    if (!smem) return VMC_ERR_ARG;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_g_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::min(nsm, 2 * Wk->W);
     if (e == cudaSuccess)
-        k_g_umma<<<dim3(Wk->W, 2), kThreads, smem, ctx->stream>>>(M, na, nb, Cf, Wk->virt_list,
-                                                                  (const float *)Wk->AinvT, (float *)Wk->G,
-                                                                  ctx->d_status, 1);
+        k_g_umma<<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Cf, Wk->pos, (const float *)Wk->AinvT,
+                                                        (float *)Wk->G, ctx->d_status, 1);
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_g_umma");

@@ -551,8 +551,7 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
         float *Cf = (float *)L->cf;
         k_convert_c<<<(M * (na + nb) + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, P->C_alpha, P->C_beta, Cf);
         ctx->launches += 1;
-        const int nvmax = M - (na < nb ? na : nb);
-        const bool umma = ctx->g_tensor_cores && nmax >= 1 && nmax <= 128 && nvmax <= 128;
+        const bool umma = ctx->g_tensor_cores && g_umma_smem(M, na, nb) > 0;
         e = cudaFuncSetAttribute(k_init_tables_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         if (e == cudaSuccess)
             k_init_tables_mixed<<<grid, VMC_THREADS, smem_m, ctx->stream>>>(
