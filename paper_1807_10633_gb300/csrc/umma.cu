@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int kM = 128;          // MMA rows (virtual slots, padded)
-constexpr int kThreads = 128;    // four warps: one per 32 tensor-memory lanes
+constexpr int kThreads = 256;    // eight warps: warp w reads tensor-memory lanes 32 (w % 4)
 constexpr unsigned kMaxSpin = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -47,6 +47,52 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, int kp4) {
 __device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
     hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
     lo = v - hi;
+}
+
+// Stages rows [0, nrows) x K [0, Kp) of a row-major FP32 matrix (leading dimension ld, valid
+// columns [0, ncols), zeros beyond) into hi/lo tiles in the K-major no-swizzle core layout.
+// Work item = one 16-byte chunk (4 K values of one row); consecutive threads take the 8 rows of a
+// core matrix, then the next core matrix along K, so a warp writes 512 contiguous bytes.
+template <int kUnroll>
+__device__ __forceinline__ void stage_tile(const float *__restrict__ src, int ld, int nrows, int ncols, int Kp,
+                                           unsigned char *hi_t, unsigned char *lo_t) {
+    const int kp4 = Kp >> 2, rg_n = (nrows + 7) >> 3;
+    const int chunks = rg_n * kp4 * 8;
+    const bool vec = (ld & 3) == 0 && (((uintptr_t)src) & 15) == 0;
+    for (int base = threadIdx.x; base < chunks; base += kUnroll * blockDim.x) {
+        float4 v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int e = base + u * blockDim.x;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < chunks) {
+                const int r8 = e & 7, cm = e >> 3, kc = cm % kp4, rg = cm / kp4;
+                const int row = rg * 8 + r8, k = kc * 4;
+                if (row < nrows) {
+                    if (vec && k + 3 < ncols) {
+                        v[u] = __ldg((const float4 *)(src + (size_t)row * ld + k));
+                    } else {
+                        float t[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) t[q] = (k + q < ncols) ? src[(size_t)row * ld + k + q] : 0.f;
+                        v[u] = make_float4(t[0], t[1], t[2], t[3]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int e = base + u * blockDim.x;
+            if (e < chunks) {
+                float4 h, l;
+                split_tf32(v[u].x, h.x, l.x); split_tf32(v[u].y, h.y, l.y);
+                split_tf32(v[u].z, h.z, l.z); split_tf32(v[u].w, h.w, l.w);
+                const uint32_t o = (uint32_t)e * 16;   // = core_off(row, k) for this chunk order
+                *(float4 *)(hi_t + o) = h;
+                *(float4 *)(lo_t + o) = l;
+            }
+        }
+    }
 }
 
 // Bounded wait on an mbarrier phase; returns false on timeout.
@@ -108,10 +154,12 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
         const int s = q >= W, w = q - s * W, n = s ? nb : na;
         float *Gw = G + (size_t)w * gstride + (s ? (size_t)(M - na) * na : 0);
         const uint16_t *pq = posb + bq * M;
-        const int c = warp * 32 + lane;
-        for (int k0 = 0; k0 < Mp; k0 += 16) {
+        const int wq = warp & 3, half = warp >> 2;
+        const int c = wq * 32 + lane;
+        const int nchunk = Mp / 16, ch0 = half ? (nchunk + 1) / 2 : 0, ch1 = half ? nchunk : (nchunk + 1) / 2;
+        for (int k0 = ch0 * 16; k0 < ch1 * 16; k0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + (uint32_t)(bq * 256) + ((uint32_t)(warp * 32) << 16) + (uint32_t)k0;
+            const uint32_t taddr = tmem + (uint32_t)(bq * 256) + ((uint32_t)(wq * 32) << 16) + (uint32_t)k0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
@@ -148,29 +196,19 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
                 __syncthreads();
             }
             const float *Cs = Cf + (s ? (size_t)M * na : 0);
-            for (int e = tid; e < Mp * Kp; e += kThreads) {
-                const int r = e / Kp, k = e - r * Kp;
-                const float v = (r < M && k < n) ? Cs[(size_t)r * n + k] : 0.0f;
-                float hi, lo;
-                split_tf32(v, hi, lo);
-                const uint32_t o = core_off(r, k, kp4);
-                *(float *)(Bh + o) = hi;
-                *(float *)(Bl + o) = lo;
+            stage_tile<2>(Cs, n, M, n, Kp, Bh, Bl);   // also zeroes rows M..ceil8(M)-1
+            const int M8 = (M + 7) & ~7;
+            for (int e = tid; e < (Mp - M8) * Kp; e += kThreads) {   // zero rows ceil8(M)..Mp-1
+                const int r = M8 + e / Kp, k = e % Kp;
+                *(float *)(Bh + core_off(r, k, kp4)) = 0.f;
+                *(float *)(Bl + core_off(r, k, kp4)) = 0.f;
             }
             cur_spin = s;
         }
         // stage A = AinvT of item t into buffer `buf`, and its orbital map
         unsigned char *Ah = Abuf + (size_t)(2 * buf) * a_bytes, *Al = Ah + a_bytes;
         const float *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
-        for (int e = tid; e < n * Kp; e += kThreads) {
-            const int r = e / Kp, k = e - r * Kp;
-            const float v = k < n ? At[(size_t)r * n + k] : 0.0f;
-            float hi, lo;
-            split_tf32(v, hi, lo);
-            const uint32_t o = core_off(r, k, kp4);
-            *(float *)(Ah + o) = hi;
-            *(float *)(Al + o) = lo;
-        }
+        stage_tile<8>(At, n, n, n, Kp, Ah, Al);
         const uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)s * M;
         for (int k = tid; k < M; k += kThreads) posb[buf * M + k] = pw[k];
         asm volatile("fence.proxy.async.shared::cta;");
