@@ -283,9 +283,14 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
 
 /* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the mixed-form refresh forms
    G = C C_occ^-1 with tcgen05 TF32 MMAs and a split-precision correction (0: FP32 CUDA cores).
-   VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256 or 512). */
+   VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256 or 512).
+   VMC_OPT_REFRESH_SMEM (default 0): 0 inverts C_occ by Gauss-Jordan elimination with the matrix
+   held in registers across a 16 x 16 thread grid, in the precision of the walker tables (FP32 for
+   VMC_MIXED, FP64 for VMC_FP64), for n_sigma <= 128; 1 uses the shared-memory kernels (mixed: LU in
+   FP64, inverse in FP32; FP64: Gauss-Jordan with row exchanges), for n_sigma <= 118. */
 #define VMC_OPT_G_TENSOR_CORES 1
 #define VMC_OPT_ELOC_THREADS 2
+#define VMC_OPT_REFRESH_SMEM 3
 vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value);
 
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */

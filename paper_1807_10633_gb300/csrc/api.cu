@@ -120,6 +120,10 @@ vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value) {
         ctx->eloc_threads = value;
         return VMC_OK;
     }
+    if (option == VMC_OPT_REFRESH_SMEM) {
+        ctx->refresh_smem = value ? 1 : 0;
+        return VMC_OK;
+    }
     return set_err(ctx, VMC_ERR_ARG, "unknown option");
 }
 

@@ -43,6 +43,7 @@ struct vmc_ctx {
     std::string rates_batch;       // walker tables the batched rate store belongs to
     int eloc_threads = 256;        // threads per local-energy CTA (set by the autotuner)
     int g_tensor_cores = 1;        // mixed refresh: G on tcgen05 (1) or CUDA cores (0)
+    int refresh_smem = 0;          // refresh: register Gauss-Jordan (0) or shared-memory LU/GJ (1)
 };
 
 // Plain-pointer view of the device lists, passed to kernels by value.

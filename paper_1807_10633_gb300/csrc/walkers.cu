@@ -376,6 +376,231 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
     }
 }
 
+// ---- Register-resident Gauss-Jordan refresh (both forms) ---------------------------------------
+// One CTA of kGJ x kGJ threads per (walker, spin).  Thread (ty, tx) keeps B[r][c] for r = ty + kGJ i,
+// c = tx + kGJ j (i, j < R) in registers; a half-warp shares tx, so the threads owning a column are
+// one half-warp and find its pivot with shuffles.  In-place elimination with implicit row pivoting:
+// step k picks the unused row p with the largest |B[p][k]|, scales row p by d = 1/B[p][k] (its k-th
+// entry becoming d), and subtracts B[r][k] times that row from every other row r (their k-th entry
+// becoming -B[r][k] d).  That is n^3 multiply-adds, two barriers per step, and no row exchanges; the
+// result X satisfies B^-1[k][piv[j]] = X[piv[k]][j].
+constexpr int kGJ = 16;
+constexpr int kNoRow = 0x7fffffff;
+
+// Orbital bookkeeping shared by the refresh kernels: occupied/virtual lists of spin sg, its
+// occupation bits and the orbital -> column/slot map.
+__device__ void refresh_orbitals(int w, int sg, int M, int na, int nb, const uint16_t *occ_list,
+                                 uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, uint16_t *s_occ,
+                                 uint16_t *s_virt, uint8_t *mark) {
+    const int n = sg ? nb : na, nv = M - n, ne = na + nb, nw = (M + 31) / 32;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const uint16_t *occ = occ_list + (size_t)w * ne + (sg ? na : 0);
+    for (int k = tid; k < M; k += nt) mark[k] = 0;
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+        s_occ[c] = occ[c];
+        mark[occ[c]] = 1;
+    }
+    __syncthreads();
+    if (warp == 0) {   // virtual slots: unoccupied orbitals ascending; occupation words
+        int v = 0;
+        for (int b0 = 0; b0 < M; b0 += 32) {
+            const int k = b0 + lane;
+            const bool occd = k < M && mark[k];
+            const unsigned bal = __ballot_sync(0xffffffffu, k < M && !occd);
+            if (k < M && !occd) s_virt[v + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)k;
+            v += __popc(bal);
+            const unsigned word = __ballot_sync(0xffffffffu, occd);
+            if (lane == 0) occ_bits[((size_t)w * 2 + sg) * nw + (b0 >> 5)] = word;
+        }
+    }
+    __syncthreads();
+    uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
+    uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)sg * M;
+    for (int s = tid; s < nv; s += nt) {
+        vl[s] = s_virt[s];
+        pw[s_virt[s]] = (uint16_t)(0x8000 | s);
+    }
+    for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
+}
+
+template <typename real, int R>
+__global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 6 ? 2 : 1))
+k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__restrict__ Cb,
+             const uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, real *G,
+             real *AinvT, unsigned *status, int do_g) {
+    constexpr int NR = kGJ * R;
+    const int w = blockIdx.x, sg = blockIdx.y;
+    const int n = sg ? nb : na, nv = M - n, ld = n + 1;
+    const real *C = sg ? Cb : Ca;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid >> 4, ty = tid & 15;
+    extern __shared__ __align__(16) unsigned char gj_smem[];
+    real *Y = (real *)gj_smem;                       // n x ld: the inverse (C_occ^T)^-1 = AinvT
+    __shared__ real pcol[2][NR], prow[2][NR], s_d[2];
+    __shared__ int s_p[2], piv[NR], rstep[NR], s_sing;
+    __shared__ uint16_t s_occ[VMC_MAX_M], s_virt[VMC_MAX_M];
+    __shared__ uint8_t mark[VMC_MAX_M];
+    if (tid == 0) s_sing = 0;
+    refresh_orbitals(w, sg, M, na, nb, occ_list, virt_list, pos_all, occ_bits, s_occ, s_virt, mark);
+    __syncthreads();
+    // B = C_occ^T: B[r][c] = C[occ[c]][r]; a half-warp reads 16 consecutive r of one orbital row
+    real X[R][R];
+    unsigned used = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (ty + kGJ * i >= n) used |= 1u << i;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int c = tx + kGJ * j;
+        const real *crow = C + (size_t)(c < n ? s_occ[c] : 0) * n;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = ty + kGJ * i;
+            X[i][j] = (r < n && c < n) ? crow[r] : real(0);
+        }
+    }
+    const unsigned hmask = 0xFFFFu << ((tx & 1) * 16);
+    for (int k = 0; k < n; ++k) {
+        const int b = k & 1, kj = k >> 4;
+        if (tx == (k & 15)) {                        // pivot search in column k (one half-warp)
+            real best = real(-1), bv = real(0);
+            int bi = kNoRow;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                real v = real(0);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (j == kj) v = X[i][j];
+                const int r = ty + kGJ * i;
+                if (r < n) pcol[b][r] = v;
+                const real a = v < real(0) ? -v : v;
+                // an unused row always wins over "none" (NaN included), so bi ends as a valid row
+                if (!((used >> i) & 1u) && (bi == kNoRow || a > best)) { best = a; bi = r; bv = v; }
+            }
+#pragma unroll
+            for (int m = 8; m >= 1; m >>= 1) {
+                const real ob = __shfl_xor_sync(hmask, best, m, 16);
+                const int oi = __shfl_xor_sync(hmask, bi, m, 16);
+                const real ov = __shfl_xor_sync(hmask, bv, m, 16);
+                if (oi != kNoRow && (bi == kNoRow || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; bv = ov; }
+            }
+            if (ty == 0) {
+                real d = bv;
+                if (d == real(0) || !isfinite(d)) { s_sing = 1; d = real(1); }
+                s_p[b] = bi;
+                s_d[b] = real(1) / d;
+                piv[k] = bi;
+                rstep[bi] = k;
+            }
+        }
+        __syncthreads();
+        const int p = s_p[b], pi = p >> 4;
+        if (ty == (p & 15)) {                        // the pivot row, scaled
+            used |= 1u << pi;
+            const real d = s_d[b];
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (i == pi) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        const int c = tx + kGJ * j;
+                        const real val = c == k ? d : X[i][j] * d;
+                        X[i][j] = val;
+                        if (c < n) prow[b][c] = val;
+                    }
+                }
+        }
+        __syncthreads();
+        real pr[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int c = tx + kGJ * j;
+            pr[j] = c < n ? prow[b][c] : real(0);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = ty + kGJ * i;
+            if (r < n && r != p) {
+                const real f = pcol[b][r];
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const real base = (tx + kGJ * j == k) ? real(0) : X[i][j];
+                    X[i][j] = fma(-f, pr[j], base);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = ty + kGJ * i;
+        if (r < n) {
+            const int yr = rstep[r] * ld;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int c = tx + kGJ * j;
+                if (c < n) Y[yr + piv[c]] = X[i][j];
+            }
+        }
+    }
+    __syncthreads();
+    const size_t gofs = (size_t)w * ((size_t)(M - na) * na + (size_t)(M - nb) * nb) +
+                        (sg ? (size_t)(M - na) * na : 0);
+    const size_t aofs = (size_t)w * ((size_t)na * na + (size_t)nb * nb) + (sg ? (size_t)na * na : 0);
+    for (int t = tid; t < n * n; t += nt) AinvT[aofs + t] = Y[(t / n) * ld + t % n];
+    if (!do_g) return;   // (mixed form) G is formed on the tensor cores by k_g_umma
+    // G[s][c] = sum_x C[virt[s]][x] AinvT[c][x]: 4 x 4 register tiles (slots x columns)
+    const int ts = (nv + 3) / 4, tc = (n + 3) / 4;
+    for (int tile = tid; tile < ts * tc; tile += nt) {
+        const int s0 = (tile / tc) * 4, c0 = (tile % tc) * 4;
+        real acc[4][4] = {};
+        const real *cr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cr[i] = C + (size_t)s_virt[min(s0 + i, nv - 1)] * n;
+        for (int x = 0; x < n; ++x) {
+            real a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = __ldg(cr[i] + x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Y[min(c0 + j, n - 1) * ld + x];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (s0 + i < nv && c0 + j < n) G[gofs + (size_t)(s0 + i) * n + c0 + j] = acc[i][j];
+    }
+}
+
+template <typename real, int R>
+cudaError_t launch_gj_r(vmc_ctx *ctx, const vmc_walkers *Wk, const real *Ca, const real *Cb, int do_g) {
+    const int na = Wk->n_alpha, nb = Wk->n_beta, nmax = na > nb ? na : nb;
+    const size_t smem = sizeof(real) * (size_t)nmax * (nmax + 1) + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_refresh_gj<real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_refresh_gj<real, R><<<dim3(Wk->W, 2), kGJ * kGJ, smem, ctx->stream>>>(
+        Wk->M, na, nb, Ca, Cb, Wk->occ_list, Wk->virt_list, Wk->pos, Wk->occ_bits, (real *)Wk->G,
+        (real *)Wk->AinvT, ctx->d_status, do_g);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_gj(vmc_ctx *ctx, const vmc_walkers *Wk, const real *Ca, const real *Cb, int do_g) {
+    const int nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
+    const int R = (nmax + kGJ - 1) / kGJ;
+    if (R <= 2) return launch_gj_r<real, 2>(ctx, Wk, Ca, Cb, do_g);
+    if (R <= 4) return launch_gj_r<real, 4>(ctx, Wk, Ca, Cb, do_g);
+    if (R == 5) return launch_gj_r<real, 5>(ctx, Wk, Ca, Cb, do_g);
+    if (R == 6) return launch_gj_r<real, 6>(ctx, Wk, Ca, Cb, do_g);
+    return launch_gj_r<real, 8>(ctx, Wk, Ca, Cb, do_g);
+}
+
 __global__ void k_convert_c(int M, int na, int nb, const double *__restrict__ Ca, const double *__restrict__ Cb,
                             float *__restrict__ Cf) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -535,12 +760,28 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
     const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
     const int nmax = na > nb ? na : nb;
     const size_t smem = sizeof(double) * ((size_t)2 * nmax * (nmax + 1) + nmax + 1);
-    if (smem > 227 * 1024) return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the in-SM inverse (max 118)");
     vmc_status st = launch_refresh_jastrow(ctx, L, P->J);
     if (st) return st;
     dim3 grid(Wk->W, 2);
     cudaError_t e;
-    if (Wk->precision == VMC_FP64) {
+    if (!ctx->refresh_smem) {
+        if (nmax > kGJ * 8) return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the register inverse (max 128)");
+        if (Wk->precision == VMC_FP64) {
+            e = launch_gj<double>(ctx, Wk, P->C_alpha, P->C_beta, 1);
+        } else {
+            float *Cf = (float *)L->cf;
+            k_convert_c<<<(M * (na + nb) + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, P->C_alpha, P->C_beta, Cf);
+            ctx->launches += 1;
+            const bool umma = ctx->g_tensor_cores && g_umma_smem(M, na, nb) > 0;
+            e = launch_gj<float>(ctx, Wk, Cf, Cf + (size_t)M * na, umma ? 0 : 1);
+            if (e == cudaSuccess && umma) {
+                vmc_status st2 = launch_g_umma(ctx, Wk, Cf);
+                if (st2) return st2;
+            }
+        }
+    } else if (smem > 227 * 1024) {
+        return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the in-SM inverse (max 118)");
+    } else if (Wk->precision == VMC_FP64) {
         e = cudaFuncSetAttribute(k_init_tables<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             k_init_tables<double><<<grid, VMC_THREADS, smem, ctx->stream>>>(

@@ -1,0 +1,70 @@
+"""Walker-table refresh (Sec. III.B): the register-resident Gauss-Jordan inverse against an FP64
+inverse of C_occ computed here, and against the shared-memory kernels, for every tile size the
+register kernel is built for (n_sigma up to 16, 64, 80, 96 and 128)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1807_10633_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+# (ring sites, n_alpha, n_beta): register tiles R = ceil(n_max / 16) in {1, 3, 5, 6, 7}
+CASES = [(20, 10, 9), (60, 40, 30), (90, 80, 75), (96, 90, 85), (98, 97, 64)]
+
+
+@pytest.fixture(scope="module")
+def vmc():
+    from paper_1807_10633_gb300 import vmc as v
+    v.lib()
+    return v
+
+
+def _tables(eng):
+    eng.sync()
+    wk = eng.walkers
+    return {k: getattr(wk, k).cpu().numpy().copy() for k in ("G", "AinvT", "occ_bits", "virt_list", "pos", "S")}
+
+
+def _expected(sys_, prm, occ):
+    """G (virtual rows, ascending orbital) and C_occ^-T per walker and spin, in FP64."""
+    M, na, nb = sys_.M, sys_.n_alpha, sys_.n_beta
+    G, A = [], []
+    for w in range(occ.shape[0]):
+        for s, C, n, o in ((0, prm.C_alpha, na, occ[w, :na]), (1, prm.C_beta, nb, occ[w, na:])):
+            if n == 0:
+                continue
+            v = np.setdiff1d(np.arange(M), o.astype(np.int64))
+            inv = np.linalg.inv(C[o.astype(np.int64)])          # C_occ^-1
+            G.append((C[v] @ inv).ravel())
+            A.append(inv.T.ravel())                              # AinvT[c][x] = (C_occ^-1)[x][c]
+    return np.concatenate(G), np.concatenate(A)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"M{c[0]}_n{c[1]}_{c[2]}")
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_register_refresh(vmc, case, precision):
+    M, na, nb = case
+    sys_ = S.hubbard(M, n_alpha=na, n_beta=nb)
+    prm = S.make_params(sys_, seed=11)
+    occ = S.init_occupations(sys_, prm, 37, seed=12)
+    eng = vmc.Engine(sys_, prm, occ, eps=1e-6, precision=precision)
+    try:
+        reg = _tables(eng)
+        G, A = _expected(sys_, prm, occ)
+        scale = max(1.0, np.abs(G).max())
+        tol = 1e-10 if precision == 0 else 2e-4
+        assert np.abs(reg["G"][:G.size] - G).max() / scale < tol
+        assert np.abs(reg["AinvT"][:A.size] - A).max() / max(1.0, np.abs(A).max()) < tol
+        if max(na, nb) <= 118:                                   # the shared-memory kernels' limit
+            for tc in ([0, 1] if precision == 1 else [1]):
+                vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, tc)
+                vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_REFRESH_SMEM, 1)
+                eng.refresh()
+                ref = _tables(eng)
+                vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_REFRESH_SMEM, 0)
+                for k in ("occ_bits", "virt_list", "pos", "S"):
+                    assert np.array_equal(reg[k], ref[k]), k
+                assert np.abs(ref["G"] - reg["G"]).max() / scale < 2 * tol
+    finally:
+        eng.close()
