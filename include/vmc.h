@@ -98,8 +98,10 @@ vmc_status vmc_lists_info(const vmc_lists *lists, int64_t *n_singles, int64_t *n
  *             row = virtual slot, column = occupied column (Eq. R: G_ac = det ratio of i->a)
  *   AinvT     real   [W][na*na + nb*nb]  (C^s_occ)^-1 transposed: AinvT[c][x]
  *   S         real   [W][2M]   Jastrow sums S_p = sum_{k occ, k != p} J_pk
- *   F         double [W][2][n_singles]  h_ai + sum_{j occ} <aj||ij> for every singles entry
- *                     (i -> a) and spin (the elements of Sec. II.A, kept up to date per move)
+ *   F         real   [W][2][ns_pad]  h_ai + sum_{j occ} <aj||ij> for every singles entry
+ *                     (i -> a) and spin (the elements of Sec. II.A, kept up to date per move;
+ *                     ns_pad = n_singles rounded up to a multiple of 4, padding entries zero;
+ *                     the mixed form recomputes them at every refresh)
  *   e_diag    double [W]       <n|H|n> including e_core
  *   rng_counter uint64 [W]     Philox counter of each walker (advanced by vmc_ctmc_step)
  * real = double for VMC_FP64, float for VMC_MIXED.  The orbital order inside occ_list and
@@ -107,7 +109,7 @@ vmc_status vmc_lists_info(const vmc_lists *lists, int64_t *n_singles, int64_t *n
  */
 typedef struct {
     int W, M, n_alpha, n_beta;
-    int precision;            /* vmc_precision of G, AinvT, S */
+    int precision;            /* vmc_precision of G, AinvT, S, F */
     uint32_t *occ_bits;
     uint16_t *occ_list;
     uint16_t *virt_list;
@@ -115,7 +117,7 @@ typedef struct {
     void *G;
     void *AinvT;
     void *S;
-    double *F;
+    void *F;
     double *e_diag;
     uint64_t *rng_counter;
 } vmc_walkers;

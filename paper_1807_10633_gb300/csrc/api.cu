@@ -157,7 +157,7 @@ vmc_status vmc_walkers_sizes(int W, int M, int na, int nb, const vmc_lists *L, i
     out[4] = (int64_t)W * (int64_t)walker_stride_G(M, na, nb);
     out[5] = (int64_t)W * (int64_t)walker_stride_A(na, nb);
     out[6] = (int64_t)W * 2 * M;
-    out[7] = (int64_t)W * 2 * (L ? L->ns : 0);
+    out[7] = (int64_t)W * 2 * (L ? (L->ns + 3) & ~(int64_t)3 : 0);
     out[8] = W;
     out[9] = W;
     return VMC_OK;

@@ -53,6 +53,7 @@ struct ListsView {
     int cpr;       // warp chunks (32 candidates) per spin-orbital row
     int n_groups;  // singles blocks of 32 spin orbitals + 2M * cpr row chunks
     int64_t ns, nds, ndo;
+    int64_t ns_pad;          // ns rounded up to a multiple of 4: row stride of the Fock tables and of F
     // singles, CSR over spatial i; records {a, w_alpha, w_beta, 0}: 16 B (mixed) or 32 B (FP64,
     // the first 8 bytes hold a)
     const uint32_t *s_off, *s_len, *s_owner;
@@ -68,8 +69,10 @@ struct ListsView {
     const uint32_t *do_off, *do_len, *do_ab, *do_owner;
     const float4 *do_rec32;
     const double4_32a *do_rec64;
-    // Fock-sum update tables: Tj[k][e] = (ai|kk), Tjk[k][e] = (ai|kk) - (ak|ki)
+    // Fock-sum update tables: Tj[k][e] = (ai|kk), Tjk[k][e] = (ai|kk) - (ak|ki), rows of ns_pad
+    // (zero padded); FP64 and FP32 copies
     const double *Tj, *Tjk;
+    const float *Tjf, *Tjkf;
     // diagonal tables: Jd[p][q] = (pp|qq), Kd[p][q] = (pq|qp); hd[p] = h_pp; h1 full
     const double *Jd, *Kd, *hd, *h1;
     double e_core;

@@ -32,6 +32,32 @@ __device__ __forceinline__ float rexp(float x) { return expf(x); }
 __device__ __forceinline__ double rrcp(double x) { return __ddiv_rn(1.0, x); }
 __device__ __forceinline__ float rrcp(float x) { return __fdiv_rn(1.0f, x); }
 
+// 16-byte vectors of the table precision, and f += sgn * x on them
+template <typename real> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
+__device__ __forceinline__ void vadd(float4 &f, float s, const float4 &x) {
+    f.x += s * x.x; f.y += s * x.y; f.z += s * x.z; f.w += s * x.w;
+}
+__device__ __forceinline__ void vadd(double2 &f, double s, const double2 &x) { f.x += s * x.x; f.y += s * x.y; }
+__device__ __forceinline__ float4 vfma2(float4 o, float x, float4 u, float y, float4 v) {   // o - x u - y v
+    o.x = o.x - x * u.x - y * v.x; o.y = o.y - x * u.y - y * v.y;
+    o.z = o.z - x * u.z - y * v.z; o.w = o.w - x * u.w - y * v.w;
+    return o;
+}
+__device__ __forceinline__ double2 vfma2(double2 o, double x, double2 u, double y, double2 v) {
+    o.x = o.x - x * u.x - y * v.x; o.y = o.y - x * u.y - y * v.y;
+    return o;
+}
+// Fock-sum table (same-spin Tjk: 1, other-spin Tj: 0) in the table precision
+template <typename real> __device__ __forceinline__ const real *fock_table(const ListsView &L, int same);
+template <> __device__ __forceinline__ const float *fock_table<float>(const ListsView &L, int same) {
+    return same ? L.Tjkf : L.Tjf;
+}
+template <> __device__ __forceinline__ const double *fock_table<double>(const ListsView &L, int same) {
+    return same ? L.Tjk : L.Tj;
+}
+
 // One packed list record (16 B in the mixed form, 32 B in the FP64 form): key (a or a|b<<16)
 // and up to three reals.
 template <typename real> struct Rec;
@@ -62,8 +88,8 @@ struct WalkerArgs {
     const uint32_t *occ_bits;
     uint16_t *occ_list, *virt_list, *pos;
     uint32_t *occ_bits_w;
-    void *G, *AinvT, *S;
-    double *F, *e_diag;
+    void *G, *AinvT, *S, *F;
+    double *e_diag;
     uint64_t *rng;
 };
 
@@ -117,7 +143,7 @@ struct View {
     const real *E;         // [2M] exp(S_p) for virtual p, 1/exp(S_p) for occupied p (nullptr: compute
                            // from S on the fly)
     const real *S;         // walker S in global (used when E == nullptr)
-    const double *F;       // walker F [2][ns]
+    const real *F;         // walker F [2][ns_pad]
     Geo geo;
     __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }              // p virtual
     __device__ real Eiv(int p) const { return E ? E[p] : rrcp(rexp(S[p])); }       // p occupied
@@ -210,7 +236,7 @@ __device__ __forceinline__ bool eval_entry(const ListsView &L, const View<real> 
         const real w = s ? r.f2() : r.f1();
         const real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), u.einv);
         ratio = rt;
-        contrib = rmul((real)V.F[(size_t)s * L.ns + idx], rt);
+        contrib = rmul(V.F[(size_t)s * L.ns_pad + idx], rt);
         A = s * M + a; B = -1;
         return true;
     }
@@ -310,7 +336,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
 
     View<real> V;
     V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
-    V.E = sE; V.S = nullptr; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+    V.E = sE; V.S = nullptr; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
     typedef typename AccT<real>::type acc_t;
     u128 q_tot = 0;
     unsigned flag = 0;
@@ -442,7 +468,7 @@ __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerAr
         const u128 Tl = T - before;   // threshold inside the group
         View<real> V;
         V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
-        V.E = nullptr; V.S = Sw; V.F = A.F + (size_t)w * 2 * L.ns; V.geo = geo;
+        V.E = nullptr; V.S = Sw; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, gsel, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -572,26 +598,31 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
     }
     // ---- Fock sums: each changed spin orbital k of spin t adds +-Tjk[k] to spin t, +-Tj[k] to the other
     {
-        double *Fw = A.F + (size_t)w * 2 * L.ns;
+        typedef typename Vec16<real>::type vec_t;
+        constexpr int VE = Vec16<real>::n;
+        const int64_t np = L.ns_pad, nvec = np / VE;
+        vec_t *F0 = (vec_t *)((real *)A.F + (size_t)w * 2 * np), *F1 = F0 + nvec;
+        const real *Tk = fock_table<real>(L, 1), *Tx = fock_table<real>(L, 0);
         const int nch = kind == 2 ? 4 : 2;
         const int chg[4] = {I, Ao, Jo, Bo};
-        for (int64_t e = tid; e < L.ns; e += nt) {
-            double f0 = Fw[e], f1 = Fw[L.ns + e];
+        for (int64_t v = tid; v < nvec; v += nt) {
+            vec_t f0 = F0[v], f1 = F1[v];
             for (int c = 0; c < nch; ++c) {
                 const int p = chg[c];
-                const double sgn = (c & 1) ? 1.0 : -1.0;
+                const real sgn = (c & 1) ? real(1) : real(-1);
                 const int t = p >= M, k = p - t * M;
-                const double jk = L.Tjk[(size_t)k * L.ns + e], jj = L.Tj[(size_t)k * L.ns + e];
-                if (t == 0) { f0 += sgn * jk; f1 += sgn * jj; }
-                else { f1 += sgn * jk; f0 += sgn * jj; }
+                const vec_t jk = __ldg((const vec_t *)(Tk + (size_t)k * np) + v);
+                const vec_t jj = __ldg((const vec_t *)(Tx + (size_t)k * np) + v);
+                if (t == 0) { vadd(f0, sgn, jk); vadd(f1, sgn, jj); }
+                else { vadd(f1, sgn, jk); vadd(f0, sgn, jj); }
             }
-            Fw[e] = f0; Fw[L.ns + e] = f1;
+            F0[v] = f0; F1[v] = f1;
         }
     }
     // ---- determinant tables: rank-1 per spin (singles, opposite-spin doubles) or rank-2
     //      Woodbury (same-spin doubles) on G and AinvT (Sherman-Morrison, Sec. III.B)
-    const int nmax = geo.na > geo.nb ? geo.na : geo.nb;
-    real *ua = vec, *ub = ua + nmax, *gci = ub + nmax, *gcj = gci + M, *ari = gcj + M, *arj = ari + nmax;
+    const int nmax = geo.na > geo.nb ? geo.na : geo.nb, np4 = (nmax + 3) & ~3, mp4 = (M + 3) & ~3;
+    real *ua = vec, *ub = ua + np4, *gci = ub + np4, *gcj = gci + mp4, *ari = gcj + mp4, *arj = ari + np4;
     int nsteps = 1;
     int sp[2], fr[2][2], to[2][2], rk[2];
     const int si = I >= M;
@@ -634,16 +665,44 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
             gci[r] = x; gcj[r] = y;
         }
         __syncthreads();
-        for (size_t t = tid; t < (size_t)nv * n; t += nt) {
-            const int r = (int)(t / n), c = (int)(t % n);
-            real old = Gs[t];
-            if (r == sa) old = (c == ci) ? (real)1 : (real)0;
-            if (rk[st] == 2 && r == sb) old = (c == cj) ? (real)1 : (real)0;
-            Gs[t] = old - gci[r] * ua[c] - gcj[r] * ub[c];
-        }
-        for (size_t t = tid; t < (size_t)n * n; t += nt) {
-            const int c = (int)(t / n), x = (int)(t % n);
-            As[t] = As[t] - ua[c] * ari[x] - ub[c] * arj[x];
+        typedef typename Vec16<real>::type vec_t;
+        constexpr int VE = Vec16<real>::n;
+        const bool rk2 = rk[st] == 2;
+        if (n % VE == 0 && n > 0 && ((((uintptr_t)Gs) | ((uintptr_t)As)) & 15) == 0) {
+            // 16-byte vectors: thread -> fixed column chunk cv, rows r0, r0 + rs, ...
+            const int nvc = n / VE, cv = tid % nvc, r0 = tid / nvc, rs = nt / nvc, c0 = cv * VE;
+            if (r0 < rs) {
+                const vec_t u = *(const vec_t *)(ua + c0), v = *(const vec_t *)(ub + c0);
+                vec_t *Gv = (vec_t *)Gs;
+#pragma unroll 4
+                for (int r = r0; r < nv; r += rs) {
+                    vec_t o = Gv[(size_t)r * nvc + cv];
+                    if (r == sa || (rk2 && r == sb)) {   // replaced row: old value is a unit vector
+                        const int cu = r == sa ? ci : cj;
+                        real *oe = (real *)&o;
+#pragma unroll
+                        for (int q = 0; q < VE; ++q) oe[q] = (c0 + q == cu) ? real(1) : real(0);
+                    }
+                    Gv[(size_t)r * nvc + cv] = vfma2(o, gci[r], u, gcj[r], v);
+                }
+                const vec_t a1 = *(const vec_t *)(ari + c0), a2 = *(const vec_t *)(arj + c0);
+                vec_t *Av = (vec_t *)As;
+#pragma unroll 4
+                for (int c = r0; c < n; c += rs)
+                    Av[(size_t)c * nvc + cv] = vfma2(Av[(size_t)c * nvc + cv], ua[c], a1, ub[c], a2);
+            }
+        } else {
+            for (size_t t = tid; t < (size_t)nv * n; t += nt) {
+                const int r = (int)(t / n), c = (int)(t % n);
+                real old = Gs[t];
+                if (r == sa) old = (c == ci) ? (real)1 : (real)0;
+                if (rk2 && r == sb) old = (c == cj) ? (real)1 : (real)0;
+                Gs[t] = old - gci[r] * ua[c] - gcj[r] * ub[c];
+            }
+            for (size_t t = tid; t < (size_t)n * n; t += nt) {
+                const int c = (int)(t / n), x = (int)(t % n);
+                As[t] = As[t] - ua[c] * ari[x] - ub[c] * arj[x];
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -731,7 +790,7 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
     (void)n_groups;
     const int nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
-    const size_t smem = 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
+    const size_t smem = 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)((nmax + 3) & ~3) + 2 * (size_t)((M + 3) & ~3));
     WalkerArgs A = make_args(Wk);
     const int sel_blocks = (Wk->W + VMC_WARPS - 1) / VMC_WARPS;
     cudaError_t e;
@@ -764,7 +823,7 @@ static size_t eloc_smem_bytes(const vmc_lists *L, const vmc_walkers *Wk) {
 static size_t apply_smem_bytes(const vmc_walkers *Wk) {
     const int M = Wk->M, nmax = Wk->n_alpha > Wk->n_beta ? Wk->n_alpha : Wk->n_beta;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
-    return 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)nmax + 2 * (size_t)M);
+    return 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)((nmax + 3) & ~3) + 2 * (size_t)((M + 3) & ~3));
 }
 
 // Builds (and uploads when changed) the descriptor table of a batch, most expensive systems

@@ -191,13 +191,17 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
         do_r64[e] = make_double4_32a(bits_d(do_ab[e]), do_vd[e], 1.0, 0.0);
     }
     // Fock tables and diagonal tables
-    std::vector<double> Tj(MM * (ns + 1)), Tjk(MM * (ns + 1)), Jd(MM * MM), Kd(MM * MM), hd(MM);
+    const int64_t ns_pad = (ns + 3) & ~(int64_t)3;
+    std::vector<double> Tj(MM * (ns_pad + 1)), Tjk(MM * (ns_pad + 1)), Jd(MM * MM), Kd(MM * MM), hd(MM);
+    std::vector<float> Tjf(MM * (ns_pad + 1)), Tjkf(MM * (ns_pad + 1));
     for (int64_t e = 0; e < ns; ++e) {
         const int i = (int)s_owner[e], a = s_a[e];
         for (int k = 0; k < M; ++k) {
             const double c = E(a, i, k, k);
-            Tj[(size_t)k * ns + e] = c;
-            Tjk[(size_t)k * ns + e] = c - E(a, k, k, i);
+            Tj[(size_t)k * ns_pad + e] = c;
+            Tjk[(size_t)k * ns_pad + e] = c - E(a, k, k, i);
+            Tjf[(size_t)k * ns_pad + e] = (float)Tj[(size_t)k * ns_pad + e];
+            Tjkf[(size_t)k * ns_pad + e] = (float)Tjk[(size_t)k * ns_pad + e];
         }
     }
     for (int p = 0; p < M; ++p) {
@@ -235,8 +239,10 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     const size_t i_do_owner = add(do_owner.data(), sizeof(uint32_t) * ndo);
     const size_t i_do_r32 = add(do_r32.data(), sizeof(float4) * ndo);
     const size_t i_do_r64 = add(do_r64.data(), sizeof(double4_32a) * ndo);
-    const size_t i_Tj = add(Tj.data(), sizeof(double) * MM * ns);
-    const size_t i_Tjk = add(Tjk.data(), sizeof(double) * MM * ns);
+    const size_t i_Tj = add(Tj.data(), sizeof(double) * MM * ns_pad);
+    const size_t i_Tjk = add(Tjk.data(), sizeof(double) * MM * ns_pad);
+    const size_t i_Tjf = add(Tjf.data(), sizeof(float) * MM * ns_pad);
+    const size_t i_Tjkf = add(Tjkf.data(), sizeof(float) * MM * ns_pad);
     const size_t i_Jd = add(Jd.data(), sizeof(double) * MM * MM);
     const size_t i_Kd = add(Kd.data(), sizeof(double) * MM * MM);
     const size_t i_hd = add(hd.data(), sizeof(double) * MM);
@@ -262,7 +268,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     }
     auto P = [&](size_t idx) { return (void *)(base + pcs[idx].off); };
     ListsView &v = L->view;
-    v.M = M; v.ns = ns; v.nds = nds; v.ndo = ndo; v.e_core = e_core;
+    v.M = M; v.ns = ns; v.nds = nds; v.ndo = ndo; v.e_core = e_core; v.ns_pad = ns_pad;
     {
         int band = 0;
         for (int t = 0; t < npair; ++t)
@@ -292,6 +298,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     v.do_ab = (const uint32_t *)P(i_do_ab); v.do_owner = (const uint32_t *)P(i_do_owner);
     v.do_rec32 = (const float4 *)P(i_do_r32); v.do_rec64 = (const double4_32a *)P(i_do_r64);
     v.Tj = (const double *)P(i_Tj); v.Tjk = (const double *)P(i_Tjk);
+    v.Tjf = (const float *)P(i_Tjf); v.Tjkf = (const float *)P(i_Tjkf);
     v.Jd = (const double *)P(i_Jd); v.Kd = (const double *)P(i_Kd);
     v.hd = (const double *)P(i_hd); v.h1 = (const double *)P(i_h1);
     L->cf = P(i_cf);

@@ -376,6 +376,50 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
     }
 }
 
+// Mixed form: the Fock sums F[s][e] = h_ai + sum_k n_k^s Tjk[k][e] + n_k^(1-s) Tj[k][e] in FP32 for
+// kFockWalkers walkers per CTA (each table row is read once per CTA), one singles entry per thread;
+// rewritten at every refresh so that the per-move FP32 updates never accumulate beyond one period.
+constexpr int kFockWalkers = 16, kFockThreads = 128;
+
+__global__ void __launch_bounds__(kFockThreads)
+k_fock_sums_f32(ListsView L, int W, const uint32_t *__restrict__ occ_bits, float *F) {
+    const int M = L.M, nw = (M + 31) / 32, w0 = blockIdx.y * kFockWalkers;
+    __shared__ float2 occf[VMC_MAX_M][kFockWalkers];   // (n_alpha, n_beta) of orbital k per walker
+    for (int t = threadIdx.x; t < M * kFockWalkers; t += blockDim.x) {
+        const int k = t / kFockWalkers, q = t % kFockWalkers, w = w0 + q;
+        float2 o = make_float2(0.f, 0.f);
+        if (w < W) {
+            const uint32_t *b = occ_bits + (size_t)w * 2 * nw;
+            o.x = (float)((b[k >> 5] >> (k & 31)) & 1u);
+            o.y = (float)((b[nw + (k >> 5)] >> (k & 31)) & 1u);
+        }
+        occf[k][q] = o;
+    }
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L.ns_pad) return;
+    const int64_t np = L.ns_pad;
+    float acc[kFockWalkers][2];
+    const float h = e < L.ns ? (float)L.h1[(size_t)L.s_a[e] * M + L.s_owner[e]] : 0.f;
+#pragma unroll
+    for (int q = 0; q < kFockWalkers; ++q) acc[q][0] = acc[q][1] = h;
+    for (int k = 0; k < M; ++k) {
+        const float tk = __ldg(L.Tjkf + (size_t)k * np + e), tx = __ldg(L.Tjf + (size_t)k * np + e);
+#pragma unroll
+        for (int q = 0; q < kFockWalkers; ++q) {
+            const float2 o = occf[k][q];
+            acc[q][0] = fmaf(o.x, tk, fmaf(o.y, tx, acc[q][0]));
+            acc[q][1] = fmaf(o.y, tk, fmaf(o.x, tx, acc[q][1]));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kFockWalkers; ++q)
+        if (w0 + q < W) {
+            F[((size_t)(w0 + q) * 2) * np + e] = acc[q][0];
+            F[((size_t)(w0 + q) * 2 + 1) * np + e] = acc[q][1];
+        }
+}
+
 // ---- Register-resident Gauss-Jordan refresh (both forms) ---------------------------------------
 // One CTA of kGJ x kGJ threads per (walker, spin).  Thread (ty, tx) keeps B[r][c] for r = ty + kGJ i,
 // c = tx + kGJ j (i, j < R) in registers; a half-warp shares tx, so the threads owning a column are
@@ -650,7 +694,7 @@ k_jastrow_sums(int W, int M, const real *__restrict__ Jsym, const uint32_t *__re
 template <typename real>
 __global__ void __launch_bounds__(VMC_THREADS)
 k_init_sums(ListsView L, int na, int nb, const real *__restrict__ Jsym, const uint16_t *occ_list,
-            real *S, double *F, double *e_diag, int full) {
+            real *S, double *F, double *e_diag, int full, int do_f) {
     const int w = blockIdx.x, M = L.M, ne = na + nb;
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_so[2 * VMC_MAX_M];   // occupied spin orbitals
@@ -660,8 +704,13 @@ k_init_sums(ListsView L, int na, int nb, const real *__restrict__ Jsym, const ui
     __syncthreads();
     (void)Jsym; (void)S;
     if (!full) return;
-    // F[s][e] = h_ai + sum_{j occ, spin s} Tjk[j][e] + sum_{j occ, other spin} Tj[j][e]
-    for (int64_t e = tid; e < L.ns; e += nt) {
+    // F[s][e] = h_ai + sum_{j occ, spin s} Tjk[j][e] + sum_{j occ, other spin} Tj[j][e]  (FP64 form)
+    for (int64_t e = tid; do_f && e < L.ns_pad; e += nt) {
+        if (e >= L.ns) {
+            F[((size_t)w * 2) * L.ns_pad + e] = 0.0;
+            F[((size_t)w * 2 + 1) * L.ns_pad + e] = 0.0;
+            continue;
+        }
         const int i = (int)L.s_owner[e], a = L.s_a[e];
         const double h = L.h1[(size_t)a * M + i];
         for (int s = 0; s < 2; ++s) {
@@ -669,9 +718,9 @@ k_init_sums(ListsView L, int na, int nb, const real *__restrict__ Jsym, const ui
             for (int c = 0; c < ne; ++c) {
                 const int js = c < na ? 0 : 1;
                 const int j = occ[c];
-                acc += (js == s ? L.Tjk : L.Tj)[(size_t)j * L.ns + e];
+                acc += (js == s ? L.Tjk : L.Tj)[(size_t)j * L.ns_pad + e];
             }
-            F[((size_t)w * 2 + s) * L.ns + e] = acc;
+            F[((size_t)w * 2 + s) * L.ns_pad + e] = acc;
         }
     }
     // e_diag = e_core + sum_p h_pp + 1/2 sum_{p != q} [(pp|qq) - delta_s (pq|qp)]
@@ -814,9 +863,16 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
     else
         k_jastrow_sums<float><<<sb, VMC_THREADS, 0, ctx->stream>>>(Wk->W, M, js32, Wk->occ_bits, (float *)Wk->S);
     ctx->launches += 1;
+    if (Wk->precision == VMC_MIXED && L->view.ns_pad > 0) {
+        dim3 fg((unsigned)((L->view.ns_pad + kFockThreads - 1) / kFockThreads),
+                (unsigned)((Wk->W + kFockWalkers - 1) / kFockWalkers));
+        k_fock_sums_f32<<<fg, kFockThreads, 0, ctx->stream>>>(L->view, Wk->W, Wk->occ_bits, (float *)Wk->F);
+        ctx->launches += 1;
+    }
     if (full) {
         k_init_sums<double><<<Wk->W, VMC_THREADS, 0, ctx->stream>>>(
-            L->view, na, nb, js64, Wk->occ_list, nullptr, Wk->F, Wk->e_diag, 1);
+            L->view, na, nb, js64, Wk->occ_list, nullptr, (double *)Wk->F, Wk->e_diag, 1,
+            Wk->precision == VMC_FP64 ? 1 : 0);
         ctx->launches += 1;
     }
     return cuda_check(ctx, cudaGetLastError(), "k_jastrow_sums/k_init_sums");

@@ -261,7 +261,7 @@ class Walkers:
         real = torch.float64 if precision == VMC_FP64 else torch.float32
         z = lambda k, dt: torch.zeros(max(1, n[k]), dtype=dt, device=device)
         return cls(W, M, na, nb, precision, z(0, torch.int32), z(1, torch.int16), z(2, torch.int16),
-                   z(3, torch.int16), z(4, real), z(5, real), z(6, real), z(7, torch.float64),
+                   z(3, torch.int16), z(4, real), z(5, real), z(6, real), z(7, real),
                    z(8, torch.float64), z(9, torch.int64))
 
     def struct(self) -> vmc_walkers:

@@ -140,6 +140,8 @@ def test_sherman_morrison_tables_equal_recomputed(vmc, precision, tol):
     for a, b in [(A1, eng.walkers.AinvT), (S1, eng.walkers.S)]:
         a = a.double().cpu().numpy(); b = b.double().cpu().numpy()
         assert np.max(np.abs(a - b)) <= tol * max(1.0, np.abs(b).max())
-    assert np.max(np.abs(F1.cpu().numpy() - eng.walkers.F.cpu().numpy())) < 1e-11
+    # F: FP64 updates are exact sums of table values; FP32 ones round at every move
+    f1, f2 = F1.double().cpu().numpy(), eng.walkers.F.double().cpu().numpy()
+    assert np.max(np.abs(f1 - f2)) < (1e-11 if precision == 0 else 2e-5 * max(1.0, np.abs(f2).max()))
     assert np.max(np.abs(E1.cpu().numpy() - eng.walkers.e_diag.cpu().numpy())) < 1e-10
     eng.close()
