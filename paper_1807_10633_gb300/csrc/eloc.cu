@@ -219,55 +219,72 @@ __device__ __forceinline__ Unit<real> shfl_unit(const Unit<real> &u, int src) {
     return v;
 }
 
-// Evaluate list entry `idx` of unit u.  Returns false if the target orbital(s) are occupied.
-// On true: ratio = psi(m)/psi(n) (in-place replacement convention, the fermionic phases of H
-// and of the ratio cancel) and contrib = H_nm * ratio.
+// Are the target orbital(s) of entry idx unoccupied?  Reads only the 2- or 4-byte key.
 template <typename real>
-__device__ __forceinline__ bool eval_entry(const ListsView &L, const View<real> &V, const Unit<real> &u,
-                                           uint32_t idx, real &ratio, real &contrib, int &A, int &B) {
+__device__ __forceinline__ bool entry_free(const ListsView &L, const View<real> &V, int kind, int cls,
+                                           uint32_t idx) {
     const int M = V.geo.M;
-    if (u.kind == 0) {
-        const int s = u.cls;
+    if (kind == 0) return V.pos[cls * M + __ldg(&L.s_a[idx])] & 0x8000;
+    if (kind == 1) {
+        const uint32_t ab = __ldg(&L.ds_ab[idx]);
+        return V.pos[cls * M + (ab & 0xFFFF)] & V.pos[cls * M + (ab >> 16)] & 0x8000;
+    }
+    const uint32_t ab = __ldg(&L.do_ab[idx]);
+    return V.pos[ab & 0xFFFF] & V.pos[M + (ab >> 16)] & 0x8000;
+}
+
+// ratio = psi(m)/psi(n) of a free entry (in-place replacement convention: the fermionic phases
+// of H and of the ratio cancel) and contrib = H_nm * ratio.  Every kernel evaluates rates with
+// this one sequence of explicitly rounded operations, so they agree bit for bit.
+template <typename real>
+__device__ __forceinline__ void entry_value(const ListsView &L, const View<real> &V, int kind, int cls, int ci,
+                                            int cj, real einv, uint32_t idx, real &ratio, real &contrib, int &A,
+                                            int &B) {
+    const int M = V.geo.M;
+    if (kind == 0) {
+        const int s = cls;
         const Rec<real> r = rec_single(L, idx, real(0));
         const int a = (int)r.key();
-        const uint16_t pa = V.pos[s * M + a];
-        if (!(pa & 0x8000)) return false;
-        const real g = V.Grow(s, pa & 0x7FFF)[u.ci];
+        const real g = V.Grow(s, V.pos[s * M + a] & 0x7FFF)[ci];
         const real w = s ? r.f2() : r.f1();
-        const real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), u.einv);
+        const real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), einv);
         ratio = rt;
         contrib = rmul(V.F[(size_t)s * L.ns_pad + idx], rt);
         A = s * M + a; B = -1;
-        return true;
+        return;
     }
-    if (u.kind == 1) {
-        const int s = u.cls;
+    if (kind == 1) {
+        const int s = cls;
         const Rec<real> r = rec_same(L, idx, real(0));
         const uint32_t ab = r.key();
         const int a = ab & 0xFFFF, b = ab >> 16;
-        const uint16_t pa = V.pos[s * M + a], pb = V.pos[s * M + b];
-        if (!(pa & pb & 0x8000)) return false;
-        const real *ra = V.Grow(s, pa & 0x7FFF);
-        const real *rb = V.Grow(s, pb & 0x7FFF);
-        const real minor = rsub(rmul(ra[u.ci], rb[u.cj]), rmul(ra[u.cj], rb[u.ci]));
+        const real *ra = V.Grow(s, V.pos[s * M + a] & 0x7FFF);
+        const real *rb = V.Grow(s, V.pos[s * M + b] & 0x7FFF);
+        const real minor = rsub(rmul(ra[ci], rb[cj]), rmul(ra[cj], rb[ci]));
         const real w = s ? r.f3() : r.f2();
-        const real rt = rmul(rmul(rmul(rmul(minor, w), V.Ev(s * M + a)), V.Ev(s * M + b)), u.einv);
+        const real rt = rmul(rmul(rmul(rmul(minor, w), V.Ev(s * M + a)), V.Ev(s * M + b)), einv);
         ratio = rt;
         contrib = rmul(r.f1(), rt);
         A = s * M + a; B = s * M + b;
-        return true;
+        return;
     }
     const Rec<real> r = rec_opp(L, idx, real(0));
     const uint32_t ab = r.key();
     const int a = ab & 0xFFFF, b = ab >> 16;
-    const uint16_t pa = V.pos[a], pb = V.pos[M + b];
-    if (!(pa & pb & 0x8000)) return false;
-    const real ga = V.Grow(0, pa & 0x7FFF)[u.ci];
-    const real gb = V.Grow(1, pb & 0x7FFF)[u.cj];
-    const real rt = rmul(rmul(rmul(rmul(rmul(ga, gb), r.f2()), V.Ev(a)), V.Ev(M + b)), u.einv);
+    const real ga = V.Grow(0, V.pos[a] & 0x7FFF)[ci];
+    const real gb = V.Grow(1, V.pos[M + b] & 0x7FFF)[cj];
+    const real rt = rmul(rmul(rmul(rmul(rmul(ga, gb), r.f2()), V.Ev(a)), V.Ev(M + b)), einv);
     ratio = rt;
     contrib = rmul(r.f1(), rt);
     A = a; B = M + b;
+}
+
+// Evaluate list entry `idx` of unit u.  Returns false if the target orbital(s) are occupied.
+template <typename real>
+__device__ __forceinline__ bool eval_entry(const ListsView &L, const View<real> &V, const Unit<real> &u,
+                                           uint32_t idx, real &ratio, real &contrib, int &A, int &B) {
+    if (!entry_free<real>(L, V, u.kind, u.cls, idx)) return false;
+    entry_value<real>(L, V, u.kind, u.cls, u.ci, u.cj, u.einv, idx, ratio, contrib, A, B);
     return true;
 }
 
@@ -305,6 +322,8 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     real *sE = sGb + (size_t)geo.nv_b * ldb;
     double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
     uint16_t *pos = (uint16_t *)(eg + n_groups);
+    // per warp: two queues of 64 entry codes (idx << 5 | unit lane): kinds 0/1, and kind 2
+    uint32_t *wq = (uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + warp * 128;
     __shared__ u128 red_q[32];
     __shared__ int next_group;
 
@@ -341,27 +360,59 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     u128 q_tot = 0;
     unsigned flag = 0;
 
-    // groups are taken dynamically; each group's sums are stored by index, so the result does not
-    // depend on which warp took it
+    // Groups are taken dynamically; each group's sums are stored by index, so the result does not
+    // depend on which warp took it.  Inside a group the warp walks the units' lists with a cheap
+    // key check and queues the entries whose targets are free; the ratio, rate and energy of
+    // queued entries are evaluated 32 at a time, one per lane, so that work is never divergent.
+    const unsigned lt_mask = (1u << lane) - 1u;
     for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
+        const int meta = act ? (u.kind | (u.cls << 2)) : 0;
         acc_t e_grp = 0;
         u128 q_grp = 0;
+        int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
+        // evaluate cnt queued entries of queue qq starting at slot q0 (lanes >= cnt idle)
+        auto drain = [&](int qq, int q0, int cnt) {
+            const uint32_t code = lane < cnt ? wq[qq * 64 + q0 + lane] : 0u;
+            const int src = code & 31;
+            const int ci = __shfl_sync(0xffffffffu, u.ci, src), cj = __shfl_sync(0xffffffffu, u.cj, src);
+            const real einv = __shfl_sync(0xffffffffu, u.einv, src);
+            const int m = __shfl_sync(0xffffffffu, meta, src);
+            if (lane < cnt) {
+                real ratio, contrib;
+                int a, b;
+                entry_value<real>(L, V, m & 3, m >> 2, ci, cj, einv, code >> 5, ratio, contrib, a, b);
+                e_grp += (acc_t)contrib;
+                q_grp += rate_of<real>(ratio, &flag);
+            }
+        };
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const Unit<real> v = shfl_unit(u, src);
-            for (uint32_t k = lane; k < v.len; k += 32) {
-                real ratio, contrib;
-                int a, b;
-                if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) {
-                    e_grp += (acc_t)contrib;
-                    q_grp += rate_of<real>(ratio, &flag);
+            const uint32_t base = __shfl_sync(0xffffffffu, u.base, src), len = __shfl_sync(0xffffffffu, u.len, src);
+            const int m = __shfl_sync(0xffffffffu, meta, src), kind = m & 3, cls = m >> 2, qq = kind == 2;
+            for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+                const uint32_t idx = base + k0 + lane;
+                const bool pass = k0 + lane < len && entry_free<real>(L, V, kind, cls, idx);
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                int q = qq ? qn1 : qn0;
+                if (pass) wq[qq * 64 + q + __popc(bal & lt_mask)] = (idx << 5) | (uint32_t)src;
+                q += __popc(bal);
+                if (q >= 32) {
+                    __syncwarp();
+                    q -= 32;
+                    drain(qq, q, 32);
+                    __syncwarp();
                 }
+                if (qq) qn1 = q; else qn0 = q;
             }
         }
+        __syncwarp();
+        if (qn0) drain(0, 0, qn0);
+        if (qn1) drain(1, 0, qn1);
+        __syncwarp();
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
         if (lane == 0) {
@@ -747,6 +798,9 @@ k_ctmc_apply_batched(const SysDesc *__restrict__ sys, int n_sys) {
 
 }  // namespace
 
+// per-warp entry queues of the local-energy kernel: 2 x 64 codes of 4 bytes
+static size_t eloc_queue_bytes(int threads) { return (size_t)(threads / 32) * 128 * sizeof(uint32_t); }
+
 static WalkerArgs make_args(vmc_walkers *Wk) {
     WalkerArgs A;
     A.W = Wk->W; A.M = Wk->M; A.na = Wk->n_alpha; A.nb = Wk->n_beta;
@@ -764,7 +818,8 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
+    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16 +
+                        eloc_queue_bytes(ctx->eloc_threads);
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e;
@@ -813,11 +868,12 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
 }
 
 // ---------------------------------------------------------------------------------- batches
-static size_t eloc_smem_bytes(const vmc_lists *L, const vmc_walkers *Wk) {
+static size_t eloc_smem_bytes(const vmc_lists *L, const vmc_walkers *Wk, int threads) {
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    return esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16;
+    return esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16 +
+           eloc_queue_bytes(threads);
 }
 
 static size_t apply_smem_bytes(const vmc_walkers *Wk) {
@@ -859,7 +915,7 @@ static vmc_status prepare_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items
         rate_off[k] = rates_total;
         rates_total += (size_t)it.walkers->W * it.lists->view.n_groups;
         tot += it.walkers->W;
-        se = std::max(se, eloc_smem_bytes(it.lists, it.walkers));
+        se = std::max(se, eloc_smem_bytes(it.lists, it.walkers, ctx->eloc_threads));
         sa = std::max(sa, apply_smem_bytes(it.walkers));
     }
     if (rates_total * sizeof(u128) > ctx->rates_bytes) {

@@ -138,6 +138,10 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     for (int t = 0; t < npair; ++t) L->h_ds_off[t + 1] = L->h_ds_off[t] + (uint32_t)dl[t].size();
     for (size_t t = 0; t < MM * MM; ++t) L->h_do_off[t + 1] = L->h_do_off[t] + (uint32_t)ol[t].size();
     const int64_t ns = L->h_s_off[M], nds = L->h_ds_off[npair], ndo = L->h_do_off[MM * MM];
+    if (ns >= (int64_t)1 << 27 || nds >= (int64_t)1 << 27 || ndo >= (int64_t)1 << 27) {
+        vmc_lists_destroy(L);
+        return set_err(ctx, VMC_ERR_ARG, "more than 2^27 entries in one list class");
+    }
     L->ns = ns; L->nds = nds; L->ndo = ndo;
     L->h_s_key = (double *)malloc(sizeof(double) * (ns + 1));
     L->h_ds_key = (double *)malloc(sizeof(double) * (nds + 1));
