@@ -169,7 +169,7 @@ template <typename real>
 __device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> &V, int g, int lane,
                                            Unit<real> &u) {
     const int M = L.M, Gs = (2 * M + 31) / 32;
-    u.len = 0;
+    u.base = 0; u.len = 0; u.kind = 0; u.cls = 0; u.ci = 0; u.cj = 0; u.i = -1; u.j = -1; u.einv = real(0);
     if (g < Gs) {
         const int i = g * 32 + lane;
         if (i >= 2 * M || !V.occ(i)) return false;
@@ -231,6 +231,25 @@ __device__ __forceinline__ bool entry_free(const ListsView &L, const View<real> 
     }
     const uint32_t ab = __ldg(&L.do_ab[idx]);
     return V.pos[ab & 0xFFFF] & V.pos[M + (ab >> 16)] & 0x8000;
+}
+
+__device__ __forceinline__ uint32_t list_size(const ListsView &L, int kind) {
+    return (uint32_t)(kind == 0 ? L.ns : (kind == 1 ? L.nds : L.ndo));
+}
+
+// Key of entry idx (a, or a | b << 16) and the occupancy test on it: the same test as entry_free,
+// split so that several keys can be loaded before any is tested.
+__device__ __forceinline__ uint32_t entry_key(const ListsView &L, int kind, uint32_t idx) {
+    if (kind == 0) return __ldg(&L.s_a[idx]);
+    return __ldg((kind == 2 ? L.do_ab : L.ds_ab) + idx);
+}
+template <typename real>
+__device__ __forceinline__ bool key_free(const View<real> &V, int kind, int cls, uint32_t key) {
+    const int M = V.geo.M;
+    const int oa = kind == 2 ? 0 : cls * M, ob = kind == 2 ? M : cls * M;
+    uint16_t x = V.pos[oa + (key & 0xFFFF)];
+    if (kind != 0) x &= V.pos[ob + (key >> 16)];
+    return x & 0x8000;
 }
 
 // ratio = psi(m)/psi(n) of a free entry (in-place replacement convention: the fermionic phases
@@ -298,6 +317,8 @@ __device__ __forceinline__ u128 rate_of(real ratio, unsigned *flag) {
     return rate_fixed(r);
 }
 
+constexpr int kWalkChunks = 4;   // 32-entry chunks whose key loads are issued together
+
 template <typename real> struct AccT { typedef double type; };
 template <> struct AccT<float> { typedef float type; };
 
@@ -306,6 +327,27 @@ __device__ __forceinline__ double warp_sum_acc(float v) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
     return (double)v;
+}
+
+// Evaluate cnt queued entries q[0..cnt) of one warp, one per lane (lanes >= cnt idle).  Entry code
+// = list index << 5 | unit lane; the unit's columns, 1/(E_i E_j) and kind | spin << 2 are held by
+// that lane (cci, ccj, ceinv, cmeta).
+template <typename real, typename acc_t>
+__device__ __forceinline__ void drain_queue(const ListsView &L, const View<real> &V, const uint32_t *q, int cnt,
+                                            int lane, int cci, int ccj, real ceinv, int cmeta, acc_t &e_grp,
+                                            u128 &q_grp, unsigned &flag) {
+    const uint32_t code = lane < cnt ? q[lane] : 0u;
+    const int src = (int)(code & 31u);
+    const int ci = __shfl_sync(0xffffffffu, cci, src), cj = __shfl_sync(0xffffffffu, ccj, src);
+    const real einv = __shfl_sync(0xffffffffu, ceinv, src);
+    const int m = __shfl_sync(0xffffffffu, cmeta, src);
+    if (lane < cnt) {
+        real ratio, contrib;
+        int a, b;
+        entry_value<real>(L, V, m & 3, m >> 2, ci, cj, einv, code >> 5, ratio, contrib, a, b);
+        e_grp += (acc_t)contrib;
+        q_grp += rate_of<real>(ratio, &flag);
+    }
 }
 
 // Local energy of walker w by the whole CTA (any number of warps).  smraw: dynamic shared memory.
@@ -331,15 +373,12 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     {
         const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
         const size_t na_el = (size_t)geo.nv_a * geo.na;
-        for (size_t t = tid; t < geo.g_stride; t += nt) {
-            const real v = Gw[t];
-            if (t < na_el) {
-                const size_t r = t / geo.na, c = t - r * geo.na;
-                sGa[r * lda + c] = v;
-            } else {
-                const size_t u = t - na_el, r = u / geo.nb, c = u - r * geo.nb;
-                sGb[r * ldb + c] = v;
-            }
+        for (int r = warp; r < geo.nv_a + geo.nv_b; r += nwarp) {   // one row per warp
+            const bool bs = r >= geo.nv_a;
+            const int rr = bs ? r - geo.nv_a : r, n = bs ? geo.nb : geo.na;
+            const real *src = Gw + (bs ? na_el + (size_t)rr * geo.nb : (size_t)rr * geo.na);
+            real *dst = bs ? sGb + (size_t)rr * ldb : sGa + (size_t)rr * lda;
+            for (int c = lane; c < n; c += 32) dst[c] = src[c];
         }
         const real *Sw = (const real *)A.S + (size_t)w * 2 * M;
         const uint16_t *pw = A.pos + (size_t)w * 2 * M;
@@ -361,57 +400,96 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     unsigned flag = 0;
 
     // Groups are taken dynamically; each group's sums are stored by index, so the result does not
-    // depend on which warp took it.  Inside a group the warp walks the units' lists with a cheap
-    // key check and queues the entries whose targets are free; the ratio, rate and energy of
-    // queued entries are evaluated 32 at a time, one per lane, so that work is never divergent.
+    // depend on which warp took it.  Inside a group the active units are compacted to the first
+    // lanes and their lists concatenated; the warp walks the concatenation 32 entries per chunk,
+    // kWalkChunks chunks at a time (their key loads in flight together), with a cheap key check,
+    // and queues the entries whose targets are free.  The ratio, rate and energy of queued entries
+    // are evaluated 32 at a time, one per lane, so that work is never divergent.
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
-        unsigned mask = __ballot_sync(0xffffffffu, act);
-        const int meta = act ? (u.kind | (u.cls << 2)) : 0;
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        const int nact = __popc(amask);
+        // lane r takes the r-th active unit: su = position of the r-th set bit of amask
+        int su = 0;
+        {
+            unsigned m = amask;
+            int k = lane;
+#pragma unroll
+            for (int wd = 16; wd >= 1; wd >>= 1) {
+                const int c = __popc(m & ((1u << wd) - 1u));
+                if (k >= c) { k -= c; m >>= wd; su += wd; }
+            }
+            if (lane >= nact) su = 0;
+        }
+        const uint32_t cbase = __shfl_sync(0xffffffffu, u.base, su);
+        const uint32_t slen = __shfl_sync(0xffffffffu, u.len, su);   // every lane shuffles
+        const uint32_t clen = lane < nact ? slen : 0u;
+        const int cmeta = __shfl_sync(0xffffffffu, u.kind | (u.cls << 2), su);
+        const int cci = __shfl_sync(0xffffffffu, u.ci, su), ccj = __shfl_sync(0xffffffffu, u.cj, su);
+        const real ceinv = __shfl_sync(0xffffffffu, u.einv, su);
+        uint32_t cend = clen;                          // inclusive scan: end of unit r's entries
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, cend, d);
+            if (lane >= d) cend += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, cend, 31);
+        const uint32_t cbme = cbase - (cend - clen);  // list index = concatenated position + cbme
         acc_t e_grp = 0;
         u128 q_grp = 0;
         int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
-        // evaluate cnt queued entries of queue qq starting at slot q0 (lanes >= cnt idle)
-        auto drain = [&](int qq, int q0, int cnt) {
-            const uint32_t code = lane < cnt ? wq[qq * 64 + q0 + lane] : 0u;
-            const int src = code & 31;
-            const int ci = __shfl_sync(0xffffffffu, u.ci, src), cj = __shfl_sync(0xffffffffu, u.cj, src);
-            const real einv = __shfl_sync(0xffffffffu, u.einv, src);
-            const int m = __shfl_sync(0xffffffffu, meta, src);
-            if (lane < cnt) {
-                real ratio, contrib;
-                int a, b;
-                entry_value<real>(L, V, m & 3, m >> 2, ci, cj, einv, code >> 5, ratio, contrib, a, b);
-                e_grp += (acc_t)contrib;
-                q_grp += rate_of<real>(ratio, &flag);
+        for (uint32_t f0 = 0; f0 < tot; f0 += 32 * kWalkChunks) {
+            uint32_t idx[kWalkChunks], key[kWalkChunks];
+            int mk[kWalkChunks], us[kWalkChunks];
+#pragma unroll
+            for (int p = 0; p < kWalkChunks; ++p) {
+                // unit of position f: the number of units ending at or before f (the ends are
+                // sorted across lanes; lanes past the active units end at tot > f)
+                const uint32_t f = f0 + 32 * p + lane;
+                int r = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, cend, r + step - 1) <= f) r += step;
+                us[p] = r;
+                mk[p] = __shfl_sync(0xffffffffu, cmeta, r);
+                idx[p] = f + __shfl_sync(0xffffffffu, cbme, r);
+                if (f >= tot) mk[p] = -1;
+                else if (idx[p] >= list_size(L, mk[p] & 3)) {   // cannot happen: guard, never read
+                    flag |= VMC_DEV_INCONSISTENT;
+                    mk[p] = -1;
+                }
             }
-        };
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const uint32_t base = __shfl_sync(0xffffffffu, u.base, src), len = __shfl_sync(0xffffffffu, u.len, src);
-            const int m = __shfl_sync(0xffffffffu, meta, src), kind = m & 3, cls = m >> 2, qq = kind == 2;
-            for (uint32_t k0 = 0; k0 < len; k0 += 32) {
-                const uint32_t idx = base + k0 + lane;
-                const bool pass = k0 + lane < len && entry_free<real>(L, V, kind, cls, idx);
-                const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                int q = qq ? qn1 : qn0;
-                if (pass) wq[qq * 64 + q + __popc(bal & lt_mask)] = (idx << 5) | (uint32_t)src;
-                q += __popc(bal);
-                if (q >= 32) {
+#pragma unroll
+            for (int p = 0; p < kWalkChunks; ++p)
+                key[p] = mk[p] < 0 ? 0u : entry_key(L, mk[p] & 3, idx[p]);
+#pragma unroll
+            for (int p = 0; p < kWalkChunks; ++p) {
+                const bool pass = mk[p] >= 0 && key_free<real>(V, mk[p] & 3, mk[p] >> 2, key[p]);
+                const bool q1 = (mk[p] & 3) == 2;
+                const uint32_t code = (idx[p] << 5) | (uint32_t)us[p];
+                const unsigned b0 = __ballot_sync(0xffffffffu, pass && !q1), b1 = __ballot_sync(0xffffffffu, pass && q1);
+                if (pass) wq[(q1 ? 64 + qn1 + __popc(b1 & lt_mask) : qn0 + __popc(b0 & lt_mask))] = code;
+                qn0 += __popc(b0);
+                qn1 += __popc(b1);
+                if (qn0 >= 32) {
                     __syncwarp();
-                    q -= 32;
-                    drain(qq, q, 32);
+                    qn0 -= 32;
+                    drain_queue<real>(L, V, wq + qn0, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
                     __syncwarp();
                 }
-                if (qq) qn1 = q; else qn0 = q;
+                if (qn1 >= 32) {
+                    __syncwarp();
+                    qn1 -= 32;
+                    drain_queue<real>(L, V, wq + 64 + qn1, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+                    __syncwarp();
+                }
             }
         }
         __syncwarp();
-        if (qn0) drain(0, 0, qn0);
-        if (qn1) drain(1, 0, qn1);
+        if (qn0) drain_queue<real>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+        if (qn1) drain_queue<real>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
         __syncwarp();
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
