@@ -317,8 +317,6 @@ __device__ __forceinline__ u128 rate_of(real ratio, unsigned *flag) {
     return rate_fixed(r);
 }
 
-constexpr int kWalkChunks = 4;   // 32-entry chunks whose key loads are issued together
-
 template <typename real> struct AccT { typedef double type; };
 template <> struct AccT<float> { typedef float type; };
 
@@ -400,91 +398,43 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     unsigned flag = 0;
 
     // Groups are taken dynamically; each group's sums are stored by index, so the result does not
-    // depend on which warp took it.  Inside a group the active units are compacted to the first
-    // lanes and their lists concatenated; the warp walks the concatenation 32 entries per chunk,
-    // kWalkChunks chunks at a time (their key loads in flight together), with a cheap key check,
-    // and queues the entries whose targets are free.  The ratio, rate and energy of queued entries
-    // are evaluated 32 at a time, one per lane, so that work is never divergent.
+    // depend on which warp took it.  Inside a group the warp walks the units' lists with a cheap
+    // key check and queues the entries whose targets are free; the ratio, rate and energy of
+    // queued entries are evaluated 32 at a time, one per lane, so that work is never divergent.
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
-        const unsigned amask = __ballot_sync(0xffffffffu, act);
-        const int nact = __popc(amask);
-        // lane r takes the r-th active unit: su = position of the r-th set bit of amask
-        int su = 0;
-        {
-            unsigned m = amask;
-            int k = lane;
-#pragma unroll
-            for (int wd = 16; wd >= 1; wd >>= 1) {
-                const int c = __popc(m & ((1u << wd) - 1u));
-                if (k >= c) { k -= c; m >>= wd; su += wd; }
-            }
-            if (lane >= nact) su = 0;
-        }
-        const uint32_t cbase = __shfl_sync(0xffffffffu, u.base, su);
-        const uint32_t slen = __shfl_sync(0xffffffffu, u.len, su);   // every lane shuffles
-        const uint32_t clen = lane < nact ? slen : 0u;
-        const int cmeta = __shfl_sync(0xffffffffu, u.kind | (u.cls << 2), su);
-        const int cci = __shfl_sync(0xffffffffu, u.ci, su), ccj = __shfl_sync(0xffffffffu, u.cj, su);
-        const real ceinv = __shfl_sync(0xffffffffu, u.einv, su);
-        uint32_t cend = clen;                          // inclusive scan: end of unit r's entries
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, cend, d);
-            if (lane >= d) cend += t;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, cend, 31);
-        const uint32_t cbme = cbase - (cend - clen);  // list index = concatenated position + cbme
+        unsigned mask = __ballot_sync(0xffffffffu, act);
+        const int cmeta = u.kind | (u.cls << 2);
+        const int cci = u.ci, ccj = u.cj;
+        const real ceinv = u.einv;
         acc_t e_grp = 0;
         u128 q_grp = 0;
         int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
-        for (uint32_t f0 = 0; f0 < tot; f0 += 32 * kWalkChunks) {
-            uint32_t idx[kWalkChunks], key[kWalkChunks];
-            int mk[kWalkChunks], us[kWalkChunks];
-#pragma unroll
-            for (int p = 0; p < kWalkChunks; ++p) {
-                // unit of position f: the number of units ending at or before f (the ends are
-                // sorted across lanes; lanes past the active units end at tot > f)
-                const uint32_t f = f0 + 32 * p + lane;
-                int r = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1)
-                    if (__shfl_sync(0xffffffffu, cend, r + step - 1) <= f) r += step;
-                us[p] = r;
-                mk[p] = __shfl_sync(0xffffffffu, cmeta, r);
-                idx[p] = f + __shfl_sync(0xffffffffu, cbme, r);
-                if (f >= tot) mk[p] = -1;
-                else if (idx[p] >= list_size(L, mk[p] & 3)) {   // cannot happen: guard, never read
-                    flag |= VMC_DEV_INCONSISTENT;
-                    mk[p] = -1;
-                }
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const uint32_t base = __shfl_sync(0xffffffffu, u.base, src), len = __shfl_sync(0xffffffffu, u.len, src);
+            const int m = __shfl_sync(0xffffffffu, cmeta, src), kind = m & 3, cls = m >> 2, qq = kind == 2;
+            if (base + len > list_size(L, kind)) {   // cannot happen: guard, never read
+                flag |= VMC_DEV_INCONSISTENT;
+                continue;
             }
-#pragma unroll
-            for (int p = 0; p < kWalkChunks; ++p)
-                key[p] = mk[p] < 0 ? 0u : entry_key(L, mk[p] & 3, idx[p]);
-#pragma unroll
-            for (int p = 0; p < kWalkChunks; ++p) {
-                const bool pass = mk[p] >= 0 && key_free<real>(V, mk[p] & 3, mk[p] >> 2, key[p]);
-                const bool q1 = (mk[p] & 3) == 2;
-                const uint32_t code = (idx[p] << 5) | (uint32_t)us[p];
-                const unsigned b0 = __ballot_sync(0xffffffffu, pass && !q1), b1 = __ballot_sync(0xffffffffu, pass && q1);
-                if (pass) wq[(q1 ? 64 + qn1 + __popc(b1 & lt_mask) : qn0 + __popc(b0 & lt_mask))] = code;
-                qn0 += __popc(b0);
-                qn1 += __popc(b1);
-                if (qn0 >= 32) {
+            for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+                const uint32_t idx = base + k0 + lane;
+                const bool pass = k0 + lane < len && entry_free<real>(L, V, kind, cls, idx);
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                int q = qq ? qn1 : qn0;
+                if (pass) wq[qq * 64 + q + __popc(bal & lt_mask)] = (idx << 5) | (uint32_t)src;
+                q += __popc(bal);
+                if (q >= 32) {
                     __syncwarp();
-                    qn0 -= 32;
-                    drain_queue<real>(L, V, wq + qn0, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+                    q -= 32;
+                    drain_queue<real>(L, V, wq + qq * 64 + q, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
                     __syncwarp();
                 }
-                if (qn1 >= 32) {
-                    __syncwarp();
-                    qn1 -= 32;
-                    drain_queue<real>(L, V, wq + 64 + qn1, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
-                    __syncwarp();
-                }
+                if (qq) qn1 = q; else qn0 = q;
             }
         }
         __syncwarp();

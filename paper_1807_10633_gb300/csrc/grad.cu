@@ -141,21 +141,44 @@ k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ pos, const r
     const size_t aoff = s ? (size_t)na * na : 0;
     const int w0 = blockIdx.y * kChunkC, w1 = min(W, w0 + kChunkC);
     const bool xin = x < n;
+    // the kRowsC map entries of a walker: two 16-byte loads when aligned (M % 8 == 0)
+    const bool vec = (M & 7) == 0 && k0 + kRowsC <= M;
+    auto map_of = [&](int w, uint4 &lo, uint4 &hi) {
+        const uint16_t *pw = pos + (size_t)w * 2 * M + (size_t)s * M + k0;
+        if (vec) {
+            lo = __ldg((const uint4 *)pw);
+            hi = __ldg((const uint4 *)pw + 1);
+        } else {
+            uint16_t t[kRowsC];
+#pragma unroll
+            for (int r = 0; r < kRowsC; ++r) t[r] = k0 + r < M ? pw[r] : (uint16_t)0x8000;
+            uint32_t q[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = (uint32_t)t[2 * k] | ((uint32_t)t[2 * k + 1] << 16);
+            lo = make_uint4(q[0], q[1], q[2], q[3]);
+            hi = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+    };
+    uint4 nlo = make_uint4(0, 0, 0, 0), nhi = nlo;
+    if (w0 < w1) map_of(w0, nlo, nhi);
     for (int w = w0; w < w1; ++w) {
+        const uint4 lo = nlo, hi = nhi;
+        if (w + 1 < w1) map_of(w + 1, nlo, nhi);    // prefetch the next walker's map
         double c0d, c1d;
         weights(mode, wgt, e, w, c0d, c1d);
         const acc_t c0 = (acc_t)c0d, c1 = (acc_t)c1d;
-        const uint16_t *pw = pos + (size_t)w * 2 * M + (size_t)s * M + k0;
         const real *A = AinvT + (size_t)w * astride + aoff;
+        const uint32_t words[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        real a[kRowsC];
+#pragma unroll
+        for (int r = 0; r < kRowsC; ++r) {         // all row loads in flight together
+            const uint32_t pc = (words[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu;
+            a[r] = (xin && k0 + r < M && !(pc & 0x8000u)) ? A[(size_t)pc * n + x] : real(0);
+        }
 #pragma unroll
         for (int r = 0; r < kRowsC; ++r) {
-            if (k0 + r >= M) break;
-            const uint16_t pc = pw[r];
-            if (!(pc & 0x8000) && xin) {
-                const acc_t a = (acc_t)A[(size_t)pc * n + x];
-                acc[r] += c0 * a;
-                if (mode) acc2[r] += c1 * a;
-            }
+            acc[r] += c0 * (acc_t)a[r];
+            if (mode) acc2[r] += c1 * (acc_t)a[r];
         }
     }
     if (!xin) return;

@@ -469,7 +469,7 @@ __device__ void refresh_orbitals(int w, int sg, int M, int na, int nb, const uin
 }
 
 template <typename real, int R>
-__global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 6 ? 2 : 1))
+__global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 5 ? 2 : 1))
 k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__restrict__ Cb,
              const uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, real *G,
              real *AinvT, unsigned *status, int do_g) {
@@ -540,9 +540,10 @@ k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__r
         }
         __syncthreads();
         const int p = s_p[b], pi = p >> 4;
-        if (ty == (p & 15)) {                        // the pivot row, scaled
+        const real d = s_d[b];
+        const bool prow_owner = ty == (p & 15), kcol_owner = tx == (k & 15);
+        if (prow_owner) {                            // the pivot row, scaled (its k-th entry: d)
             used |= 1u << pi;
-            const real d = s_d[b];
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (i == pi) {
@@ -556,7 +557,8 @@ k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__r
                 }
         }
         __syncthreads();
-        real pr[R];
+        // every other row: X[r][c] -= B[r][k] prow[c]; then the column-k owners set X[r][k] = -B[r][k] d
+        real pr[R], f[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int c = tx + kGJ * j;
@@ -565,14 +567,20 @@ k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__r
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = ty + kGJ * i;
-            if (r < n && r != p) {
-                const real f = pcol[b][r];
+            f[i] = (r < n && r != p) ? pcol[b][r] : real(0);
+        }
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const real base = (tx + kGJ * j == k) ? real(0) : X[i][j];
-                    X[i][j] = fma(-f, pr[j], base);
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int j = 0; j < R; ++j) X[i][j] = fma(-f[i], pr[j], X[i][j]);
+        if (kcol_owner) {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (ty + kGJ * i != p) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (j == kj) X[i][j] = -f[i] * d;
                 }
-            }
         }
     }
     __syncthreads();
