@@ -356,6 +356,11 @@ def singles_counts(sys_, eps):
     return cnt
 
 
+def cpu_sample_default() -> int:
+    """Walkers in the oracle sample: 8 per host core (at most 16 cores), about 10-20 s at H160."""
+    return 8 * max(1, min(os.cpu_count() or 1, 16))
+
+
 def cpu_baseline(args, sys_, prm, occ, sample: int):
     import oracle
     nt = os.cpu_count() or 1
@@ -393,7 +398,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        sample = args.cpu_sample or max(1, min(os.cpu_count() or 1, 16))
+        sample = args.cpu_sample or cpu_sample_default()
         vals = []
         for _ in range(args.steps):
             vals.append(cpu_baseline(args, sys_, prm, occ, sample))
@@ -444,7 +449,7 @@ def main():
     if not args.no_batch:
         line["batched_uneven"] = run_batch(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = args.cpu_sample or max(1, min(os.cpu_count() or 1, 16))
+        sample = args.cpu_sample or cpu_sample_default()
         line["cpu_baseline"] = cpu_baseline(args, sys_, prm, occ, sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
