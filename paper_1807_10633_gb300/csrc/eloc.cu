@@ -237,21 +237,6 @@ __device__ __forceinline__ uint32_t list_size(const ListsView &L, int kind) {
     return (uint32_t)(kind == 0 ? L.ns : (kind == 1 ? L.nds : L.ndo));
 }
 
-// Key of entry idx (a, or a | b << 16) and the occupancy test on it: the same test as entry_free,
-// split so that several keys can be loaded before any is tested.
-__device__ __forceinline__ uint32_t entry_key(const ListsView &L, int kind, uint32_t idx) {
-    if (kind == 0) return __ldg(&L.s_a[idx]);
-    return __ldg((kind == 2 ? L.do_ab : L.ds_ab) + idx);
-}
-template <typename real>
-__device__ __forceinline__ bool key_free(const View<real> &V, int kind, int cls, uint32_t key) {
-    const int M = V.geo.M;
-    const int oa = kind == 2 ? 0 : cls * M, ob = kind == 2 ? M : cls * M;
-    uint16_t x = V.pos[oa + (key & 0xFFFF)];
-    if (kind != 0) x &= V.pos[ob + (key >> 16)];
-    return x & 0x8000;
-}
-
 // ratio = psi(m)/psi(n) of a free entry (in-place replacement convention: the fermionic phases
 // of H and of the ratio cancel) and contrib = H_nm * ratio.  Every kernel evaluates rates with
 // this one sequence of explicitly rounded operations, so they agree bit for bit.
@@ -327,24 +312,61 @@ __device__ __forceinline__ double warp_sum_acc(float v) {
     return (double)v;
 }
 
-// Evaluate cnt queued entries q[0..cnt) of one warp, one per lane (lanes >= cnt idle).  Entry code
-// = list index << 5 | unit lane; the unit's columns, 1/(E_i E_j) and kind | spin << 2 are held by
-// that lane (cci, ccj, ceinv, cmeta).
-template <typename real, typename acc_t>
+// Evaluate cnt queued entries q[0..cnt) of one warp, one per lane (lanes >= cnt idle).  Every entry
+// of one queue has the same kind K (compile time).  Entry code = list index << 5 | unit lane; the
+// unit's columns, 1/(E_i E_j) and kind | spin << 2 are held by that lane (cci, ccj, ceinv, cmeta).
+template <int K, typename real, typename acc_t>
 __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real> &V, const uint32_t *q, int cnt,
                                             int lane, int cci, int ccj, real ceinv, int cmeta, acc_t &e_grp,
                                             u128 &q_grp, unsigned &flag) {
     const uint32_t code = lane < cnt ? q[lane] : 0u;
     const int src = (int)(code & 31u);
-    const int ci = __shfl_sync(0xffffffffu, cci, src), cj = __shfl_sync(0xffffffffu, ccj, src);
+    const int ci = __shfl_sync(0xffffffffu, cci, src);
+    const int cj = K == 0 ? 0 : __shfl_sync(0xffffffffu, ccj, src);
     const real einv = __shfl_sync(0xffffffffu, ceinv, src);
-    const int m = __shfl_sync(0xffffffffu, cmeta, src);
+    const int cls = K == 2 ? 0 : (__shfl_sync(0xffffffffu, cmeta, src) >> 2);
     if (lane < cnt) {
         real ratio, contrib;
         int a, b;
-        entry_value<real>(L, V, m & 3, m >> 2, ci, cj, einv, code >> 5, ratio, contrib, a, b);
+        entry_value<real>(L, V, K, cls, ci, cj, einv, code >> 5, ratio, contrib, a, b);
         e_grp += (acc_t)contrib;
         q_grp += rate_of<real>(ratio, &flag);
+    }
+}
+
+// Walk the list of one unit of kind K (lanes over entries, 32 per chunk): load the 2- or 4-byte key,
+// test the target orbital(s) in the shared orbital map and queue the free entries; every 32 queued
+// entries are evaluated at once.  Lanes past the end test `sent`, a key naming the unit's own
+// (occupied) orbitals, so the test needs no bounds branch.  pos and the queue are addressed as
+// 32-bit shared-memory addresses.
+template <int K, typename real, typename acc_t>
+__device__ __forceinline__ void walk_unit(const ListsView &L, const View<real> &V, uint32_t base, uint32_t len,
+                                          int cls, int src, uint32_t sent, uint32_t *wq, int &q, int lane,
+                                          unsigned lt_mask, int cci, int ccj, real ceinv, int cmeta, acc_t &e_grp,
+                                          u128 &q_grp, unsigned &flag) {
+    const int M = V.geo.M;
+    const uint32_t sA = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? 0 : cls * M));
+    const uint32_t sB = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? M : cls * M));
+    const uint32_t sQ = (uint32_t)__cvta_generic_to_shared(wq);
+    for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+        const uint32_t idx = base + k0 + lane;
+        uint32_t key = sent;
+        if (k0 + lane < len) key = K == 0 ? (uint32_t)__ldg(&L.s_a[idx]) : __ldg((K == 2 ? L.do_ab : L.ds_ab) + idx);
+        uint32_t x, y = 0xFFFFu;
+        asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sA + 2u * (key & 0xFFFFu)));
+        if (K != 0) asm("ld.shared.u16 %0, [%1];" : "=r"(y) : "r"(sB + 2u * (key >> 16)));
+        const bool pass = x & y & 0x8000u;
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (pass)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ + 4u * (uint32_t)(q + __popc(bal & lt_mask))),
+                         "r"((idx << 5) | (uint32_t)src) : "memory");
+        q += __popc(bal);
+        if (q >= 32) {
+            __syncwarp();
+            q -= 32;
+            drain_queue<K, real, acc_t>(L, V, wq + q, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+            __syncwarp();
+        }
     }
 }
 
@@ -355,7 +377,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
                                             u128 *__restrict__ rates, unsigned *status, unsigned char *smraw) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarp = nt >> 5;
-    const int M = geo.M, n_groups = L.n_groups;
+    const int M = geo.M, n_groups = L.n_groups, n_sgl_groups = (2 * M + 31) / 32;
     const int lda = geo.na + 1, ldb = geo.nb + 1;    // padded rows: no bank conflicts on columns
     real *sGa = (real *)smraw;
     real *sGb = sGa + (size_t)geo.nv_a * lda;
@@ -412,34 +434,42 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
         acc_t e_grp = 0;
         u128 q_grp = 0;
         int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
+        // key naming the unit's own orbitals (occupied): the test of lanes past the end of a list
+        uint32_t csent = 0;
+        if (act) {
+            if (u.kind == 0) csent = (uint32_t)(u.i - u.cls * M);
+            else if (u.kind == 1) csent = (uint32_t)(u.i - u.cls * M) | ((uint32_t)(u.j - u.cls * M) << 16);
+            else csent = (uint32_t)u.i | ((uint32_t)(u.j - M) << 16);
+        }
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
             const uint32_t base = __shfl_sync(0xffffffffu, u.base, src), len = __shfl_sync(0xffffffffu, u.len, src);
-            const int m = __shfl_sync(0xffffffffu, cmeta, src), kind = m & 3, cls = m >> 2, qq = kind == 2;
+            const int m = __shfl_sync(0xffffffffu, cmeta, src), kind = m & 3, cls = m >> 2;
+            const uint32_t sent = __shfl_sync(0xffffffffu, csent, src);
             if (base + len > list_size(L, kind)) {   // cannot happen: guard, never read
                 flag |= VMC_DEV_INCONSISTENT;
                 continue;
             }
-            for (uint32_t k0 = 0; k0 < len; k0 += 32) {
-                const uint32_t idx = base + k0 + lane;
-                const bool pass = k0 + lane < len && entry_free<real>(L, V, kind, cls, idx);
-                const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                int q = qq ? qn1 : qn0;
-                if (pass) wq[qq * 64 + q + __popc(bal & lt_mask)] = (idx << 5) | (uint32_t)src;
-                q += __popc(bal);
-                if (q >= 32) {
-                    __syncwarp();
-                    q -= 32;
-                    drain_queue<real>(L, V, wq + qq * 64 + q, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
-                    __syncwarp();
-                }
-                if (qq) qn1 = q; else qn0 = q;
-            }
+            if (kind == 2)
+                walk_unit<2, real, acc_t>(L, V, base, len, cls, src, sent, wq + 64, qn1, lane, lt_mask, cci, ccj,
+                                          ceinv, cmeta, e_grp, q_grp, flag);
+            else if (kind == 1)
+                walk_unit<1, real, acc_t>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj, ceinv,
+                                          cmeta, e_grp, q_grp, flag);
+            else
+                walk_unit<0, real, acc_t>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj, ceinv,
+                                          cmeta, e_grp, q_grp, flag);
         }
         __syncwarp();
-        if (qn0) drain_queue<real>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
-        if (qn1) drain_queue<real>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+        // queue 0 holds singles (singles groups) or same-spin doubles (row groups); queue 1 opposite spin
+        if (qn0) {
+            if (g < n_sgl_groups)
+                drain_queue<0, real, acc_t>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+            else
+                drain_queue<1, real, acc_t>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+        }
+        if (qn1) drain_queue<2, real, acc_t>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
         __syncwarp();
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
