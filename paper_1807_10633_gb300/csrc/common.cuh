@@ -50,8 +50,10 @@ struct vmc_ctx {
 struct ListsView {
     int M;
     int band;      // largest |p - q| with a non-empty double list (pair candidates of a row)
-    int cpr;       // warp chunks (32 candidates) per spin-orbital row
-    int n_groups;  // singles blocks of 32 spin orbitals + 2M * cpr row chunks
+    int cpr;       // warp chunks (32 candidates) per alpha row
+    int rpg;       // beta rows per group (their candidates are the band's same-spin q only)
+    int cpr_b;     // warp chunks per beta row when rpg == 1
+    int n_groups;  // singles blocks of 32 spin orbitals + M * cpr alpha-row chunks + beta groups
     int64_t ns, nds, ndo;
     int64_t ns_pad;          // ns rounded up to a multiple of 4: row stride of the Fock tables and of F
     // singles, CSR over spatial i; records {a, w_alpha, w_beta, 0}: 16 B (mixed) or 32 B (FP64,

@@ -4,10 +4,11 @@
 // slot map are staged in shared memory; the screened lists (shared by all walkers, L2-resident)
 // are streamed per occupied pair.  Work is split into "groups" in canonical move order:
 //   singles : blocks of 32 consecutive spin orbitals i; unit = occupied i, list = singles(i)
-//   doubles : one group per spin-orbital row i (warp chunks of 32 candidates if needed); the
-//             candidates j > i of a row are the spin orbitals whose spatial index lies within
+//   doubles : one group per alpha spin-orbital row i (warp chunks of 32 candidates if needed);
+//             the candidates j > i of a row are the spin orbitals whose spatial index lies within
 //             the band of non-empty pair lists (same spin: q in (p, p+B]; alpha rows also
-//             opposite spin q in [p-B, p+B]), so a row fits one warp for local orbitals.
+//             opposite spin q in [p-B, p+B]), so a row fits one warp for local orbitals.  Beta
+//             rows have only the B same-spin candidates; floor(32 / B) of them share a group.
 // A warp takes one group; its active units (i and j occupied, list non-empty) are walked in
 // order with the lanes over each unit's list entries.  Each group's CTMC rates are summed as
 // exact 128-bit fixed-point integers (order independent) and stored; the CTMC kernel re-walks
@@ -180,10 +181,25 @@ __device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> 
         u.einv = V.Eiv(i);
         return u.len > 0;
     }
-    const int r = (g - Gs) / L.cpr, chunk = (g - Gs) - r * L.cpr;
-    const int i = r;
+    // alpha rows: cpr groups each; beta rows: rpg rows per group (lane = row offset * band +
+    // candidate), or cpr_b groups each.  Groups and lanes run in ascending (i, j) order.
+    const int ga = g - Gs;
+    int i, t;
+    if (ga < M * L.cpr) {
+        const int chunk = ga % L.cpr;
+        i = ga / L.cpr;
+        t = chunk * 32 + lane;
+    } else if (L.rpg > 1) {
+        const int ro = lane / L.band;
+        i = M + (ga - M * L.cpr) * L.rpg + ro;
+        t = lane - ro * L.band;
+        if (ro >= L.rpg || i >= 2 * M) return false;
+    } else {
+        const int gb = ga - M * L.cpr, chunk = gb % L.cpr_b;
+        i = M + gb / L.cpr_b;
+        t = chunk * 32 + lane;
+    }
     if (!V.occ(i)) return false;
-    const int t = chunk * 32 + lane;
     if (t >= row_ncand(L, i)) return false;
     const int j = row_cand(L, i, t);
     if (!V.occ(j)) return false;

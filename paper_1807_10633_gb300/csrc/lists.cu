@@ -290,7 +290,11 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
         const int cand = std::min(band, M - 1) + std::min(2 * band + 1, M);
         v.band = band;
         v.cpr = any_double ? std::max(1, (cand + 31) / 32) : 0;
-        v.n_groups = (2 * M + 31) / 32 + 2 * M * v.cpr;
+        // beta rows have at most `band` candidates: 32 / band of them share one warp group
+        v.rpg = (band >= 1 && band <= 32) ? 32 / band : 1;
+        v.cpr_b = band <= 32 ? 1 : (band + 31) / 32;
+        const int nb_groups = (!any_double || band == 0) ? 0 : (v.rpg > 1 ? (M + v.rpg - 1) / v.rpg : M * v.cpr_b);
+        v.n_groups = (2 * M + 31) / 32 + M * v.cpr + nb_groups;
     }
     v.s_off = (const uint32_t *)P(i_s_off); v.s_len = (const uint32_t *)P(i_s_len);
     v.s_owner = (const uint32_t *)P(i_s_owner); v.s_a = (const uint16_t *)P(i_s_a);
