@@ -286,13 +286,18 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
 /* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the mixed-form refresh forms
    G = C C_occ^-1 with tcgen05 TF32 MMAs and a split-precision correction (0: FP32 CUDA cores).
    VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256 or 512).
-   VMC_OPT_REFRESH_SMEM (default 0): 0 inverts C_occ by Gauss-Jordan elimination with the matrix
-   held in registers across a 16 x 16 thread grid, in the precision of the walker tables (FP32 for
-   VMC_MIXED, FP64 for VMC_FP64), for n_sigma <= 128; 1 uses the shared-memory kernels (mixed: LU in
-   FP64, inverse in FP32; FP64: Gauss-Jordan with row exchanges), for n_sigma <= 118. */
+   VMC_OPT_MIXED_REFRESH_GJ32 (default 0): how VMC_MIXED recomputes C_occ^-1 at every refresh.
+   0: LU with partial pivoting in FP64 in shared memory, the inverse from the factors and G in
+   FP32 (the recompute is FP64, the tables FP32; n_sigma <= 128).  1: Gauss-Jordan elimination in
+   FP32 with the matrix held in registers across a 16 x 16 thread grid (n_sigma <= 128), about
+   4x faster on GB300, whose FP64 rate is 1/64 of its FP32 rate.
+   VMC_OPT_REFRESH_SMEM (default 0): 1 replaces the register Gauss-Jordan kernels by the
+   shared-memory kernels (mixed: the FP64 LU above; FP64: Gauss-Jordan with row exchanges,
+   n_sigma <= 118); the FP64 form's default is the register Gauss-Jordan in FP64. */
 #define VMC_OPT_G_TENSOR_CORES 1
 #define VMC_OPT_ELOC_THREADS 2
 #define VMC_OPT_REFRESH_SMEM 3
+#define VMC_OPT_MIXED_REFRESH_GJ32 4
 vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value);
 
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */

@@ -124,6 +124,10 @@ vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value) {
         ctx->refresh_smem = value ? 1 : 0;
         return VMC_OK;
     }
+    if (option == VMC_OPT_MIXED_REFRESH_GJ32) {
+        ctx->mixed_gj32 = value ? 1 : 0;
+        return VMC_OK;
+    }
     return set_err(ctx, VMC_ERR_ARG, "unknown option");
 }
 

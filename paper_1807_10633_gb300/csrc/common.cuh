@@ -44,6 +44,7 @@ struct vmc_ctx {
     int eloc_threads = 256;        // threads per local-energy CTA (set by the autotuner)
     int g_tensor_cores = 1;        // mixed refresh: G on tcgen05 (1) or CUDA cores (0)
     int refresh_smem = 0;          // refresh: register Gauss-Jordan (0) or shared-memory LU/GJ (1)
+    int mixed_gj32 = 0;            // mixed refresh: FP64 LU of C_occ (0) or FP32 register Gauss-Jordan (1)
 };
 
 // Plain-pointer view of the device lists, passed to kernels by value.

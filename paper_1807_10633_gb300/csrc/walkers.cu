@@ -821,7 +821,10 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
     if (st) return st;
     dim3 grid(Wk->W, 2);
     cudaError_t e;
-    if (!ctx->refresh_smem) {
+    // register Gauss-Jordan: the FP64 form, or the mixed form when FP32 elimination is asked for;
+    // otherwise the shared-memory kernels (mixed: FP64 LU, FP32 inverse from the factors)
+    const bool reg = !ctx->refresh_smem && (Wk->precision == VMC_FP64 || ctx->mixed_gj32);
+    if (reg) {
         if (nmax > kGJ * 8) return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the register inverse (max 128)");
         if (Wk->precision == VMC_FP64) {
             e = launch_gj<double>(ctx, Wk, P->C_alpha, P->C_beta, 1);
@@ -836,8 +839,10 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
                 if (st2) return st2;
             }
         }
-    } else if (smem > 227 * 1024) {
+    } else if (Wk->precision == VMC_FP64 && smem > 227 * 1024) {
         return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the in-SM inverse (max 118)");
+    } else if (Wk->precision == VMC_MIXED && nmax > VMC_MAX_M / 2) {   // per-thread staging array bound
+        return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the in-SM FP64 LU (max 128)");
     } else if (Wk->precision == VMC_FP64) {
         e = cudaFuncSetAttribute(k_init_tables<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)

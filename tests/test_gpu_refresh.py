@@ -1,6 +1,7 @@
-"""Walker-table refresh (Sec. III.B): the register-resident Gauss-Jordan inverse against an FP64
-inverse of C_occ computed here, and against the shared-memory kernels, for every tile size the
-register kernel is built for (n_sigma up to 16, 64, 80, 96 and 128)."""
+"""Walker-table refresh (Sec. III.B): the register-resident Gauss-Jordan inverse (FP64 form; FP32
+option of the mixed form) against an FP64 inverse of C_occ computed here, and against the
+shared-memory kernels (the mixed form's default FP64 LU), for every tile size the register kernel is
+built for (n_sigma up to 16, 64, 80, 96 and 128)."""
 import numpy as np
 import pytest
 import torch
@@ -50,6 +51,9 @@ def test_register_refresh(vmc, case, precision):
     occ = S.init_occupations(sys_, prm, 37, seed=12)
     eng = vmc.Engine(sys_, prm, occ, eps=1e-6, precision=precision)
     try:
+        if precision == 1:   # the mixed form's register kernel is the FP32 Gauss-Jordan option
+            vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 1)
+            eng.refresh()
         reg = _tables(eng)
         G, A = _expected(sys_, prm, occ)
         scale = max(1.0, np.abs(G).max())
@@ -59,10 +63,16 @@ def test_register_refresh(vmc, case, precision):
         if max(na, nb) <= 118:                                   # the shared-memory kernels' limit
             for tc in ([0, 1] if precision == 1 else [1]):
                 vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, tc)
-                vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_REFRESH_SMEM, 1)
+                if precision == 1:   # the mixed default: FP64 LU in shared memory
+                    vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 0)
+                else:
+                    vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_REFRESH_SMEM, 1)
                 eng.refresh()
                 ref = _tables(eng)
                 vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_REFRESH_SMEM, 0)
+                if precision == 1:
+                    vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 1)
+                    assert np.abs(ref["AinvT"][:A.size] - A).max() / max(1.0, np.abs(A).max()) < tol
                 for k in ("occ_bits", "virt_list", "pos", "S"):
                     assert np.array_equal(reg[k], ref[k]), k
                 assert np.abs(ref["G"] - reg["G"]).max() / scale < 2 * tol

@@ -17,8 +17,11 @@ def vmc():
     return v
 
 
-def _check(vmc, sys_, prm, occ, eps, precision, idx=None, eps_run=None, tol=1e-10):
+def _check(vmc, sys_, prm, occ, eps, precision, idx=None, eps_run=None, tol=1e-10, gj32=0):
     eng = vmc.Engine(sys_, prm, occ, eps=eps, precision=precision)
+    if gj32:   # mixed form with the FP32 Gauss-Jordan refresh instead of the FP64 LU
+        vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 1)
+        eng.refresh()
     e, t = eng.local_energy(eps_run)
     eng.sync()
     e = e.cpu().numpy()
@@ -60,9 +63,10 @@ def test_hubbard_2d_4x4(vmc):
     _check(vmc, sys_, prm, occ, 0.0, 0)
 
 
-def test_h80_mixed_form_mEh_per_particle(vmc):
+@pytest.mark.parametrize("gj32", [0, 1], ids=["lu64", "gj32"])
+def test_h80_mixed_form_mEh_per_particle(vmc, gj32):
     sys_, prm, occ = make_case("H80", 2048)
-    e, ref = _check(vmc, sys_, prm, occ, 1e-6, 1, idx=np.arange(0, 2048, 97))
+    e, ref = _check(vmc, sys_, prm, occ, 1e-6, 1, idx=np.arange(0, 2048, 97), gj32=gj32)
     print("H80 mixed max |dE| per particle (mEh):", 1e3 * np.max(np.abs(e - ref)) / sys_.n_elec)
 
 
