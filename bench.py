@@ -10,8 +10,10 @@ One timed step = one optimisation iteration of the method: `sweeps` CTMC sweeps,
 then the energy gradient, one AMSGrad update (Eqs. m1-m2) and the FP64 recompute of every
 walker's tables for the new parameters (Sec. III.B).  value = walkers * sweeps / step time.
 
-The mixed-precision form gives `value`; the FP64 form is measured the same way and reported
-under "fp64_form".  `--impl reference` times the FP64 CPU oracle instead (a bounded sample).
+The mixed-precision form gives `value` (FP32 tables and ratios, C_occ factorised by FP64 LU at each
+refresh, G on the tensor cores); the FP64 form ("fp64_form") and the mixed form with an FP32
+Gauss-Jordan refresh ("mixed_gj32_form") are measured the same way.  `--impl reference` times
+the FP64 CPU oracle instead (a bounded sample).
 """
 from __future__ import annotations
 
@@ -46,7 +48,9 @@ def parse():
     ap.add_argument("--walkers", type=int, default=32768)
     ap.add_argument("--sweeps", type=int, default=8, help="CTMC sweeps per optimisation iteration")
     ap.add_argument("--eps", type=float, default=1e-6)
-    ap.add_argument("--forms", default="mixed,fp64")
+    ap.add_argument("--forms", default="mixed,fp64,mixed_gj32",
+                    help="mixed: FP32 tables, FP64 LU of C_occ at every refresh; fp64: FP64 throughout; "
+                         "mixed_gj32: FP32 tables, FP32 Gauss-Jordan refresh")
     ap.add_argument("--cpu-sample", type=int, default=0, help="walkers in the oracle sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
@@ -54,6 +58,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven batched workload")
     ap.add_argument("--g-cuda-cores", action="store_true", help="form G on CUDA cores instead of tcgen05")
     ap.add_argument("--batch-walkers", type=int, default=2048)
+    ap.add_argument("--eps-sweep", default="", help="comma-separated eps values: run the eps / size study "
+                    "(cost per 1000 samples of H chains) instead of the benchmark")
+    ap.add_argument("--study-systems", default="H20,H40,H80,H160")
     return ap.parse_args()
 
 
@@ -119,6 +126,43 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ncu counters of one k_local_energy launch (mixed form, H160, eps 1e-6), per walker: DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum) and L2 bytes (lts__t_sectors.sum x 32), from the
+# capture summarised in profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel
+# source with this digest only; any later change of the kernel reports traffic as null.
+ELOC_COUNTERS = {"sha256": "e7227f9b36f194ad212838d6159a9572af19dee012e7dfcfd22695677303939d",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 79589.8, "l2_bytes_per_walker": 776666.9}
+
+
+def eloc_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    h.update((ROOT / "paper_1807_10633_gb300" / "csrc" / "eloc.cu").read_bytes())
+    return h.hexdigest()
+
+
+def l2_probe_gbs(dev) -> float:
+    """L2 bandwidth probe: copy between two 24 MB buffers that stay in the 129 MB L2 (read + write bytes)."""
+    import torch
+    n = 24 * 1024 * 1024 // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(5):
+        t0.record()
+        for _ in range(20):
+            b.copy_(a)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / 20
+        best = ms if best is None else min(best, ms)
+    return 2 * a.numel() * 4 / (best * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -128,28 +172,31 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------- our arm
-def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
+def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     import torch
     from paper_1807_10633_gb300 import vmc
 
-    dev = torch.device("cuda", 0)
+    from paper_1807_10633_gb300 import dist as D
+
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)               # every library call of the step runs here
     stream.wait_stream(torch.cuda.current_stream(dev))
     torch.cuda.set_stream(stream)
-    eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=0, stream=stream)
+    eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=dev.index, stream=stream)
     if args.g_cuda_cores:
         vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, 0)
+    if gj32:   # mixed tables, C_occ inverted by FP32 Gauss-Jordan at every refresh
+        vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 1)
+        eng.refresh()
     W, N2, M = eng.W, 2 * sys_.M, sys_.M
     n_singles, n_same, n_opp = vmc.vmc_lists_info(eng.lists)
     eloc_threads = vmc.Batch([eng]).autotune()    # threads per walker CTA for the local energy
     np_ = eng.n_params
     f64 = dict(dtype=torch.float64, device=dev)
-    AO = torch.zeros(np_, **f64)
-    AEO = torch.zeros(np_, **f64)
+    red, AO, AEO, sums = D.sums_buffer(np_, dev)   # the walker sums: one buffer, one exchange
     g = torch.zeros(np_, **f64)
     m1 = torch.zeros(np_, **f64)
     m2 = torch.zeros(np_, **f64)
-    sums = torch.zeros(2, **f64)
     AOv, AEOv = eng.split(AO), eng.split(AEO)
     ws = eng.walkers.struct()
     prm_s = eng.params
@@ -160,10 +207,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
     ev_pairs = []   # (start, end) events around vmc_local_energy
     seed = args.seed
 
-    def step(timed: bool, e2e: bool, it: int):
-        if e2e:
-            eng.p.copy_(p_host, non_blocking=True)
-        AO.zero_(); AEO.zero_(); sums.zero_()
+    def sweeps(timed: bool, it: int):
+        red.zero_()
         for s in range(args.sweeps):
             if timed:
                 a = torch.cuda.Event(enable_timing=True)
@@ -174,28 +219,43 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
                 b.record(stream)
                 ev_pairs.append((a, b))
             vmc.vmc_accumulate_gradient(eng.ctx, ws, eng.t_res, eng.e_loc, AOv, AEOv, sums)
-            vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm_s, ws, seed + it, eng.moves)
+            vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm_s, ws, D.rank_seed(seed + it, rank), eng.moves)
+
+    def update():
         vmc.vmc_energy_gradient(eng.ctx, sums, AO, AEO, g)
         vmc.vmc_amsgrad_update(eng.ctx, eng.p, g, m1, m2, 0.001, 0.1, 0.01)
         vmc.vmc_walkers_refresh(eng.ctx, eng.lists, prm_s, ws)
+
+    def step(timed: bool, e2e: bool, it: int):
+        if e2e:
+            eng.p.copy_(p_host, non_blocking=True)
+        sweeps(timed, it)
+        D.allreduce_sums(red)                    # N > 1: the one exchange of the iteration
+        update()
         if e2e:
             out_host[:np_].copy_(eng.p, non_blocking=True)
             out_host[np_:].copy_(sums, non_blocking=True)
             stream.synchronize()                 # the host needs the result before its next step
             p_host.copy_(out_host[:np_])
 
-    graph = None
+    graph = None          # one graph per step (N = 1), or sweeps and update around the exchange
+    graph_b = None
     graph_launches = 0
     if not args.no_graph:
-        l0 = vmc.vmc_launch_count(eng.ctx)
         step(timed=False, e2e=False, it=0)        # every workspace exists before capture
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
         l1 = vmc.vmc_launch_count(eng.ctx)
-        with torch.cuda.graph(graph, stream=stream):
-            step(timed=False, e2e=False, it=0)
+        if world == 1:
+            with torch.cuda.graph(graph, stream=stream):
+                step(timed=False, e2e=False, it=0)
+        else:
+            with torch.cuda.graph(graph, stream=stream):
+                sweeps(False, 0)
+            graph_b = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph_b, stream=stream):
+                update()
         graph_launches = vmc.vmc_launch_count(eng.ctx) - l1      # kernels in one captured step
-        del l0
 
     def run_step(timed: bool, e2e: bool, it: int):
         if graph is None or timed:
@@ -204,6 +264,9 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt):
         if e2e:
             eng.p.copy_(p_host, non_blocking=True)
         graph.replay()
+        if graph_b is not None:
+            D.allreduce_sums(red)
+            graph_b.replay()
         if e2e:
             out_host[:np_].copy_(eng.p, non_blocking=True)
             out_host[np_:].copy_(sums, non_blocking=True)
@@ -290,7 +353,7 @@ def run_batch(args):
     import torch
     from paper_1807_10633_gb300 import vmc
 
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)
     stream.wait_stream(torch.cuda.current_stream(dev))
     torch.cuda.set_stream(stream)
@@ -299,7 +362,7 @@ def run_batch(args):
         sys_ = load_system(name)
         prm = S.make_params(sys_, seed=args.seed)
         occ = S.init_occupations(sys_, prm, args.batch_walkers, seed=args.seed + 1)
-        engines.append(vmc.Engine(sys_, prm, occ, eps=eps, precision=vmc.VMC_MIXED, device=0, stream=stream))
+        engines.append(vmc.Engine(sys_, prm, occ, eps=eps, precision=vmc.VMC_MIXED, device=dev.index, stream=stream))
     b = vmc.Batch(engines)
     threads = b.autotune()
     f64 = dict(dtype=torch.float64, device=dev)
@@ -345,6 +408,62 @@ def run_batch(args):
     return res
 
 
+def eps_study(args):
+    """Cost per 1000 samples (local energy + CTMC move, mixed form) against eps and chain length,
+    and the fitted exponent of cost per sample against the number of orbitals at each eps."""
+    import torch
+    from paper_1807_10633_gb300 import vmc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    eps_list = [float(e) for e in args.eps_sweep.split(",") if e.strip()]
+    rows = []
+    for name in [x.strip() for x in args.study_systems.split(",") if x.strip()]:
+        sys_ = load_system(name)
+        prm = S.make_params(sys_, seed=args.seed)
+        occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1)
+        for eps in eps_list:
+            eng = vmc.Engine(sys_, prm, occ, eps=eps, precision=vmc.VMC_MIXED, device=dev.index, stream=stream)
+            vmc.Batch([eng]).autotune()
+            ns, nd, no = vmc.vmc_lists_info(eng.lists)
+            ws, prm_s = eng.walkers.struct(), eng.params
+
+            def sweep(k):
+                vmc.vmc_local_energy(eng.ctx, eng.lists, prm_s, ws, eps, eng.e_loc, eng.t_res)
+                vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm_s, ws, args.seed + k, eng.moves)
+            for k in range(3):
+                sweep(k)
+            eng.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            n_sw = max(2, args.sweeps)
+            a.record(stream)
+            for k in range(n_sw):
+                sweep(100 + k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            eng.sync()
+            ms = a.elapsed_time(b) / n_sw
+            e_mean = float((eng.t_res * eng.e_loc).sum() / eng.t_res.sum())
+            rows.append({"system": name, "M": sys_.M, "eps": eps, "walkers": args.walkers,
+                         "lists": {"singles": ns, "same": nd, "opposite": no},
+                         "ms_per_sweep": ms, "ms_per_1000_samples": 1000.0 * ms / args.walkers,
+                         "energy_per_electron": e_mean / sys_.n_elec})
+            print(json.dumps(rows[-1]), flush=True)
+            eng.close()
+            del eng
+            torch.cuda.empty_cache()
+    fits = {}
+    for eps in eps_list:
+        pts = [(r["M"], r["ms_per_1000_samples"]) for r in rows if r["eps"] == eps]
+        if len(pts) >= 2:
+            x = np.log([p[0] for p in pts]); y = np.log([p[1] for p in pts])
+            fits[f"{eps:g}"] = float(np.polyfit(x, y, 1)[0])
+    print(json.dumps({"study": "eps_and_size", "unit": "ms per 1000 samples (local energy + CTMC move)",
+                      "form": "mixed", "rows": len(rows), "exponent_vs_orbitals": fits}), flush=True)
+
+
 def singles_counts(sys_, eps):
     """Length of every spatial singles list at eps (used for the byte count only)."""
     e = sys_.eri
@@ -384,15 +503,22 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
+    if args.eps_sweep:
+        if rank == 0:
+            eps_study(args)
+        return
     config = {"workload": f"{args.system} chain STO-3G 1.8 bohr Loewdin, eps={args.eps:g}, "
                           f"{args.walkers} walkers/GPU, {args.sweeps} CTMC sweeps per optimisation step",
               "walkers_per_gpu": args.walkers, "sweeps_per_step": args.sweeps, "eps": args.eps,
               "l2": "inputs larger than L2 (walker state > 1 GB)",
-              "launch": "eager" if args.no_graph else "one CUDA graph per optimisation step"}
+              "launch": "eager" if args.no_graph else "one CUDA graph per optimisation step",
+              "parallelism": (f"walkers sharded over {world} GPUs, one all-reduce of the walker sums per "
+                              f"optimisation step, parameters replicated") if world > 1 else "1 GPU"}
 
     sys_ = load_system(args.system)
     prm = S.make_params(sys_, seed=args.seed)
-    occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1)
+    # each rank's own walkers (weak scaling: walkers per GPU fixed); rank 0 keeps the 1-GPU inputs
+    occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1 + 1000003 * rank)
     s_cnt = singles_counts(sys_, args.eps)
 
     if args.impl == "reference":
@@ -419,10 +545,15 @@ def main():
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     results = {}
     for f in forms:
-        results[f] = run_form(args, sys_, prm, occ, vmc.VMC_MIXED if f == "mixed" else vmc.VMC_FP64, rank, world,
-                              s_cnt)
+        results[f] = run_form(args, sys_, prm, occ, vmc.VMC_FP64 if f == "fp64" else vmc.VMC_MIXED, rank, world,
+                              s_cnt, gj32=(f == "mixed_gj32"))
     head = results.get("mixed") or results[forms[0]]
     peak, peak_kind = measured_peaks()
+    counters_ok = ("mixed" in results and eloc_source_digest() == ELOC_COUNTERS["sha256"]
+                   and args.system == ELOC_COUNTERS["system"] and args.eps == ELOC_COUNTERS["eps"])
+    traffic = ELOC_COUNTERS["dram_bytes_per_walker"] * args.walkers if counters_ok else None
+    l2_peak = l2_probe_gbs(torch.device("cuda", 0))
+    l2_bytes = ELOC_COUNTERS["l2_bytes_per_walker"] * args.walkers if counters_ok else None
     scale = world
     line = {"metric": METRIC, "value": head["value"] * scale, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -434,8 +565,14 @@ def main():
             "eloc_threads_per_walker_cta": head["eloc_threads"],
             "roofline": {"kernel": "k_local_energy", "bound": "hbm", "achieved": head["eloc_gbs"],
                          "peak": peak, "unit": "GB/s", "frac": head["eloc_gbs"] / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind, "traffic": traffic,
                          "bytes_per_launch": head["eloc_bytes"], "launch_ms": head["eloc_ms"]},
+            "l2_roofline": {"kernel": "k_local_energy", "bound": "l2",
+                            "achieved": (l2_bytes / (head["eloc_ms"] * 1e-3) / 1e9) if l2_bytes else None,
+                            "peak": l2_peak, "unit": "GB/s",
+                            "frac": (l2_bytes / (head["eloc_ms"] * 1e-3) / 1e9 / l2_peak) if l2_bytes else None,
+                            "bytes": "ncu lts__t_sectors x 32 per launch, scaled by walkers",
+                            "peak_source": "24 MB L2-resident copy probe (read + write)"},
             "clocks": head["clocks"],
             "energy_per_electron": head["energy"] / sys_.n_elec,
             "lists": head["lists"], "n_params": head["n_params"]}

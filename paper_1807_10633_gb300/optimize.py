@@ -1,0 +1,119 @@
+"""The optimisation loop of the method (Sec. II.C): every iteration samples the wavefunction with
+`sweeps` rejection-free CTMC steps of all walkers (Sec. II.B), accumulates the residence-time
+weighted sums of Eq. (vmc) and the gradient pieces of Eq. (grad), forms the energy gradient
+g = 2 (<E_L O> - <E_L><O>), applies one AMSGrad step (Eqs. m1-m2, beta1 = 0.1, beta2 = 0.01) and
+recomputes the walker tables for the new parameters.  The step size starts at 0.001 and is raised to
+0.01 after the first iterations, as in the paper's hydrogen-chain runs (Sec. IV.B).
+
+Orchestration only: every step runs in the CUDA library through its C ABI.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import torch
+
+from . import dist as D
+from . import vmc
+
+
+@dataclass
+class Iteration:
+    index: int
+    alpha: float
+    energy: float              # sum t E_L / sum t over the iteration's samples (Eq. vmc)
+    energy_per_electron: float
+    t_sum: float
+    grad_norm: float
+    ms: float                  # device time of the iteration (CUDA events)
+
+
+def alpha_schedule(k: int, alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5) -> float:
+    """Step size of iteration k: alpha0 for the first `warm` iterations, then alpha1."""
+    return alpha0 if k < warm else alpha1
+
+
+def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_in: int = 0,
+             alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5, beta1: float = 0.1,
+             beta2: float = 0.01, n_elec: int | None = None, callback=None) -> list[Iteration]:
+    """Run n_iter AMSGrad iterations on `eng` (its parameters eng.p are updated in place).
+
+    Each iteration: `sweeps` CTMC steps; the first `burn_in` of them move the walkers without
+    entering the sums.  Under an initialised process group the walker sums of all ranks are added
+    before the gradient is formed, so every rank applies the same update.
+    """
+    if sweeps <= burn_in:
+        raise ValueError("sweeps must exceed burn_in")
+    dev = eng.p.device
+    stream = torch.cuda.current_stream(dev)
+    np_ = eng.n_params
+    red, AO, AEO, sums = D.sums_buffer(np_, dev)
+    g = torch.zeros(np_, dtype=torch.float64, device=dev)
+    m = torch.zeros_like(g)
+    v = torch.zeros_like(g)
+    AOv, AEOv = eng.split(AO), eng.split(AEO)
+    ne = n_elec or (eng.na + eng.nb)
+    rank = 0
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        rank = torch.distributed.get_rank()
+    out = []
+    for k in range(n_iter):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        red.zero_()
+        ws = eng.walkers.struct()
+        prm = eng.params
+        for s in range(sweeps):
+            vmc.vmc_local_energy(eng.ctx, eng.lists, prm, ws, eng.eps, eng.e_loc, eng.t_res)
+            if s >= burn_in:
+                vmc.vmc_accumulate_gradient(eng.ctx, ws, eng.t_res, eng.e_loc, AOv, AEOv, sums)
+            vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm, ws, D.rank_seed(seed + k, rank), eng.moves)
+        D.allreduce_sums(red)
+        alpha = alpha_schedule(k, alpha0, alpha1, warm)
+        vmc.vmc_energy_gradient(eng.ctx, sums, AO, AEO, g)
+        vmc.vmc_amsgrad_update(eng.ctx, eng.p, g, m, v, alpha, beta1, beta2)
+        vmc.vmc_walkers_refresh(eng.ctx, eng.lists, prm, ws)
+        b.record(stream)
+        eng.sync()
+        T, TE = (float(x) for x in sums.cpu())
+        it = Iteration(k, alpha, TE / T, TE / T / ne, T, float(g.norm()), a.elapsed_time(b))
+        out.append(it)
+        if callback is not None:
+            callback(it)
+    return out
+
+
+def main():
+    import argparse
+    import json
+
+    from . import systems as S
+    ap = argparse.ArgumentParser(description="AMSGrad optimisation of a Jastrow-Slater wavefunction on one GPU")
+    ap.add_argument("--system", default="H20")
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--sweeps", type=int, default=16)
+    ap.add_argument("--burn-in", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
+    args = ap.parse_args()
+    sys_ = S.named_system(args.system)
+    prm = S.make_params(sys_, seed=args.seed)
+    occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1)
+    eng = vmc.Engine(sys_, prm, occ, eps=args.eps,
+                     precision=vmc.VMC_MIXED if args.form == "mixed" else vmc.VMC_FP64)
+    vmc.Batch([eng]).autotune()
+    t0 = time.perf_counter()
+    its = optimize(eng, args.iters, args.sweeps, seed=args.seed, burn_in=args.burn_in, n_elec=sys_.n_elec,
+                   callback=lambda it: print(json.dumps(it.__dict__), flush=True))
+    print(json.dumps({"system": args.system, "walkers": args.walkers, "sweeps": args.sweeps,
+                      "form": args.form, "eps": args.eps, "wall_s": time.perf_counter() - t0,
+                      "first": its[0].energy_per_electron, "last": its[-1].energy_per_electron}))
+    eng.close()
+
+
+if __name__ == "__main__":
+    main()
