@@ -294,13 +294,27 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
             for (int r = k + 1 + lane; r < n; r += 32) B[r * ld + k] *= dinv;
         }
         __syncthreads();
-        for (int r = k + 1 + warp; r < n; r += (nt >> 5)) {
-            const double l = B[r * ld + k];
-            for (int c = k + 1 + lane; c < n; c += 32) B[r * ld + c] -= l * B[k * ld + c];
+        // trailing update B[r][c] -= B[r][k] B[k][c] over the (n-k-1)^2 block, flattened so that
+        // every lane of every warp has an element (the FP64 pipe is the bound here)
+        const int wdt = n - k - 1, tot = wdt * wdt;
+        if (tid < tot) {
+            const int sr = nt / wdt, sc = nt - sr * wdt;   // advance of the flat index by nt
+            int rr = tid / wdt, cc = tid - rr * wdt;
+            const double *rowk = B + k * ld + k + 1;
+            for (int t = tid; t < tot; t += nt) {
+                double *rowr = B + (k + 1 + rr) * ld;
+                rowr[k + 1 + cc] = fma(-rowr[k], rowk[cc], rowr[k + 1 + cc]);
+                cc += sc; rr += sr;
+                if (cc >= wdt) { cc -= wdt; ++rr; }
+            }
         }
         __syncthreads();
     }
     if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
+    // reciprocals of U's diagonal (one FP64 division per row, not per element; n <= 128)
+    __shared__ double rdiag[VMC_MAX_M / 2];
+    for (int r = tid; r < n; r += nt) rdiag[r] = 1.0 / B[r * ld + r];
+    __syncthreads();
     // ---- FP32 copies: unit-lower L, unit-upper U' = D^-1 U, and 1/D; the buffer is reused
     {
         const int per = (n * n + nt - 1) / nt;
@@ -309,7 +323,7 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         for (int t = tid; t < n * n && cnt < per; t += nt, ++cnt) {
             const int r = t / n, c = t % n;
             const double v = B[r * ld + c];
-            vals[cnt] = c > r ? (float)(v / B[r * ld + r]) : (c == r ? (float)(1.0 / v) : (float)v);
+            vals[cnt] = c > r ? (float)(v * rdiag[r]) : (c == r ? (float)rdiag[r] : (float)v);
         }
         __syncthreads();
         cnt = 0;
