@@ -69,6 +69,9 @@ k_weight_prep(int W, const double *__restrict__ t, const double *__restrict__ e,
 
 // dJ partials: tile (P, Q) of 32 x 32 spin orbitals with P <= Q, walker chunk blockIdx.y.
 // Exact 64-bit integer sums of the fixed-point weights.  part layout: [n_out][chunk][N2][N2].
+// The chunk's 32-orbital occupation windows and weights are staged in shared memory; lane l of
+// warp v owns p = 32P + l and q = 32Q + 4v .. 4v + 3, so the q bits are warp-uniform (a branch)
+// and the p bit is a mask.
 __global__ void __launch_bounds__(256)
 k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const long long *__restrict__ cq, int mode,
          long long *__restrict__ part) {
@@ -76,28 +79,59 @@ k_grad_J(int W, int M, const uint32_t *__restrict__ bits, const long long *__res
     int t = blockIdx.x, P = 0;
     while (t >= T - P) { t -= T - P; ++P; }
     const int Q = P + t;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int pl = tid >> 3, ql0 = (tid & 7) * 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    __shared__ uint2 s_b[kChunkJ];
+    __shared__ longlong2 s_c[kChunkJ];
+    const int w0 = blockIdx.y * kChunkJ, nwk = min(W, w0 + kChunkJ) - w0;
+    if ((M & 31) == 0) {   // windows are whole words of one spin
+        const int wp = P * 32 < M ? P : nw + (P * 32 - M) / 32, wq = Q * 32 < M ? Q : nw + (Q * 32 - M) / 32;
+        for (int i = tid; i < nwk; i += blockDim.x) {
+            const uint32_t *bw = bits + (size_t)(w0 + i) * 2 * nw;
+            s_b[i] = make_uint2(bw[wp], bw[wq]);
+        }
+    } else {
+        for (int i = warp; i < nwk; i += nwarp) {
+            const uint32_t *bw = bits + (size_t)(w0 + i) * 2 * nw;
+            const uint32_t bp = window_bits(bw, M, nw, P * 32, lane);
+            const uint32_t bq = window_bits(bw, M, nw, Q * 32, lane);
+            if (lane == 0) s_b[i] = make_uint2(bp, bq);
+        }
+    }
+    for (int i = tid; i < nwk; i += blockDim.x) {
+        longlong2 c;
+        c.x = cq[w0 + i];
+        c.y = mode ? cq[W + w0 + i] : 0;
+        s_c[i] = c;
+    }
+    __syncthreads();
+    const int qb = warp * 4;
     long long acc[4] = {0, 0, 0, 0}, acc2[4] = {0, 0, 0, 0};
-    const int w0 = blockIdx.y * kChunkJ, w1 = min(W, w0 + kChunkJ);
-    for (int w = w0; w < w1; ++w) {
-        const uint32_t *bw = bits + (size_t)w * 2 * nw;
-        const uint32_t bp = window_bits(bw, M, nw, P * 32, lane);
-        const uint32_t bq = window_bits(bw, M, nw, Q * 32, lane);
-        if ((bp >> pl) & 1u) {
-            const long long c0 = cq[w], c1 = mode ? cq[W + w] : 0;
+    if (mode) {
+        for (int i = 0; i < nwk; ++i) {
+            const uint2 b = s_b[i];
+            const longlong2 c = s_c[i];
+            const long long m = -(long long)((b.x >> lane) & 1u);
+            const long long c0 = c.x & m, c1 = c.y & m;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if ((bq >> (ql0 + k)) & 1u) { acc[k] += c0; acc2[k] += c1; }
+                if ((b.y >> (qb + k)) & 1u) { acc[k] += c0; acc2[k] += c1; }
+        }
+    } else {
+        for (int i = 0; i < nwk; ++i) {
+            const uint2 b = s_b[i];
+            const long long c0 = s_c[i].x & -(long long)((b.x >> lane) & 1u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((b.y >> (qb + k)) & 1u) acc[k] += c0;
         }
     }
     const size_t chunk_sz = (size_t)N2 * N2;
     long long *dst = part + (size_t)blockIdx.y * chunk_sz;
     long long *dst2 = part + ((size_t)gridDim.y + blockIdx.y) * chunk_sz;
-    const int p = P * 32 + pl;
+    const int p = P * 32 + lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int q = Q * 32 + ql0 + k;
+        const int q = Q * 32 + qb + k;
         if (p < N2 && q < N2 && p <= q) {
             dst[(size_t)p * N2 + q] = acc[k];
             if (mode) dst2[(size_t)p * N2 + q] = acc2[k];

@@ -260,60 +260,71 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         }
         for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
     }
-    // ---- LU with partial pivoting, FP64: P B = L U.  Per column: warp 0 finds the pivot, swaps
-    //      the rows and scales the multipliers; then all threads update the trailing block.
-    for (int k = 0; k < n; ++k) {
-        if (warp == 0) {
-            double best = -1.0;
-            int idx = k;
-            for (int r = k + lane; r < n; r += 32) {
-                const double v = fabs(B[r * ld + k]);
-                if (v > best) { best = v; idx = r; }
-            }
+    // ---- LU with partial pivoting, FP64: P B = L U, rows left in place (row list rl: rl[k] = the
+    //      row that is pivot k).  Look-ahead: while warps 1.. update columns k+2.. of step k, warp 0
+    //      updates column k+1, picks the pivot of step k+1 into the other row list and scales its
+    //      multipliers, so the serial pivot work overlaps the FP64 update.
+    __shared__ int perm2[VMC_MAX_M];
+    auto pivot = [&](int k, const int *rin, int *rout) {      // warp 0 only
+        for (int r = lane; r < n; r += 32) rout[r] = rin[r];
+        __syncwarp();
+        double best = -1.0;
+        int idx = k;
+        for (int r = k + lane; r < n; r += 32) {
+            const double v = fabs(B[rout[r] * ld + k]);
+            if (v > best) { best = v; idx = r; }
+        }
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, m);
-                const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
-                if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
-            }
-            if (idx != k) {
-                for (int c = lane; c < n; c += 32) {
-                    const double t = B[k * ld + c];
-                    B[k * ld + c] = B[idx * ld + c];
-                    B[idx * ld + c] = t;
-                }
-                if (lane == 0) { const int t = perm[k]; perm[k] = perm[idx]; perm[idx] = t; }
+        for (int m = 16; m >= 1; m >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, m);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
+            if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+        }
+        if (lane == 0 && idx != k) { const int t = rout[k]; rout[k] = rout[idx]; rout[idx] = t; }
+        __syncwarp();
+        double d = B[rout[k] * ld + k];
+        if (d == 0.0) {
+            if (lane == 0) s_sing = 1;
+            d = 1.0;
+        }
+        const double dinv = 1.0 / d;
+        for (int r = k + 1 + lane; r < n; r += 32) B[rout[r] * ld + k] *= dinv;
+    };
+    if (n > 0 && warp == 0) pivot(0, perm, perm2);
+    __syncthreads();
+    int *cur = perm2, *nxt = perm;
+    for (int k = 0; k + 1 < n; ++k) {
+        const double *rowk = B + cur[k] * ld;
+        if (warp == 0) {
+            for (int r = k + 1 + lane; r < n; r += 32) {
+                double *row = B + cur[r] * ld;
+                row[k + 1] = fma(-row[k], rowk[k + 1], row[k + 1]);
             }
             __syncwarp();
-            double d = B[k * ld + k];
-            if (d == 0.0) {
-                if (lane == 0) s_sing = 1;
-                d = 1.0;
-            }
-            const double dinv = 1.0 / d;
-            for (int r = k + 1 + lane; r < n; r += 32) B[r * ld + k] *= dinv;
-        }
-        __syncthreads();
-        // trailing update B[r][c] -= B[r][k] B[k][c] over the (n-k-1)^2 block, flattened so that
-        // every lane of every warp has an element (the FP64 pipe is the bound here)
-        const int wdt = n - k - 1, tot = wdt * wdt;
-        if (tid < tot) {
-            const int sr = nt / wdt, sc = nt - sr * wdt;   // advance of the flat index by nt
-            int rr = tid / wdt, cc = tid - rr * wdt;
-            const double *rowk = B + k * ld + k + 1;
-            for (int t = tid; t < tot; t += nt) {
-                double *rowr = B + (k + 1 + rr) * ld;
-                rowr[k + 1 + cc] = fma(-rowr[k], rowk[cc], rowr[k + 1 + cc]);
-                cc += sc; rr += sr;
-                if (cc >= wdt) { cc -= wdt; ++rr; }
+            pivot(k + 1, cur, nxt);
+        } else {
+            // B[r][c] -= B[r][k] B[pivot k][c] for the unused rows r and c >= k+2, flattened over
+            // warps 1.. so that every lane has an element (the FP64 pipe is the bound here)
+            const int wr = n - k - 1, wc = n - k - 2, tot = wr * wc, t0 = tid - 32, nth = nt - 32;
+            if (wc > 0 && t0 < tot) {
+                const int sr = nth / wc, sc = nth - sr * wc;   // advance of the flat index by nth
+                int rr = t0 / wc, cc = t0 - rr * wc;
+                for (int t = t0; t < tot; t += nth) {
+                    double *row = B + cur[k + 1 + rr] * ld;
+                    row[k + 2 + cc] = fma(-row[k], rowk[k + 2 + cc], row[k + 2 + cc]);
+                    cc += sc; rr += sr;
+                    if (cc >= wc) { cc -= wc; ++rr; }
+                }
             }
         }
         __syncthreads();
+        int *t = cur; cur = nxt; nxt = t;
     }
+    const int *rl = cur;
     if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
     // reciprocals of U's diagonal (one FP64 division per row, not per element; n <= 128)
     __shared__ double rdiag[VMC_MAX_M / 2];
-    for (int r = tid; r < n; r += nt) rdiag[r] = 1.0 / B[r * ld + r];
+    for (int r = tid; r < n; r += nt) rdiag[r] = 1.0 / B[rl[r] * ld + r];
     __syncthreads();
     // ---- FP32 copies: unit-lower L, unit-upper U' = D^-1 U, and 1/D; the buffer is reused
     {
@@ -322,7 +333,7 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         int cnt = 0;
         for (int t = tid; t < n * n && cnt < per; t += nt, ++cnt) {
             const int r = t / n, c = t % n;
-            const double v = B[r * ld + c];
+            const double v = B[rl[r] * ld + c];
             vals[cnt] = c > r ? (float)(v * rdiag[r]) : (c == r ? (float)rdiag[r] : (float)v);
         }
         __syncthreads();
@@ -330,7 +341,7 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         for (int t = tid; t < n * n && cnt < per; t += nt, ++cnt) {
             const int r = t / n, c = t % n;
             LUf[r * ld + c] = vals[cnt];
-            Y[r * ld + c] = perm[r] == c ? 1.0f : 0.0f;      // rows of the permutation
+            Y[r * ld + c] = rl[r] == c ? 1.0f : 0.0f;        // rows of the permutation
         }
         __syncthreads();
     }
