@@ -531,6 +531,7 @@ def main():
         v = statistics.median(x["value"] for x in vals)
         cb = dict(vals[0])
         cb["value"] = v
+        config = dict(config, launch="FP64 CPU oracle, OpenMP over walkers", l2="not applicable (CPU)")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
