@@ -216,9 +216,10 @@ vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n_items, const vmc_batch_ite
 vmc_status vmc_ctmc_step_batch(vmc_ctx *ctx, int n_items, const vmc_batch_item *items, uint64_t seed);
 
 /*
- * Autotuner for the local-energy launch: times 128, 256 and 512 threads per walker CTA on the
- * given items (two launches each, CUDA events on the context's stream), keeps the fastest for
- * later vmc_local_energy / vmc_local_energy_batch calls on this context and returns it.
+ * Autotuner for the local-energy launch: times 128, 256, 384 and 512 threads per walker CTA on the
+ * given items (two launches each, CUDA events on the context's stream; vmc_local_energy for one
+ * item, vmc_local_energy_batch for several), keeps the fastest for later vmc_local_energy /
+ * vmc_local_energy_batch calls on this context and returns it.
  */
 vmc_status vmc_autotune_local_energy(vmc_ctx *ctx, int n_items, const vmc_batch_item *items,
                                      int *threads_out);
@@ -285,7 +286,7 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
 
 /* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the mixed-form refresh forms
    G = C C_occ^-1 with tcgen05 TF32 MMAs and a split-precision correction (0: FP32 CUDA cores).
-   VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256 or 512).
+   VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256, 384 or 512).
    VMC_OPT_MIXED_REFRESH_GJ32 (default 0): how VMC_MIXED recomputes C_occ^-1 at every refresh.
    0: LU with partial pivoting in FP64 in shared memory, the inverse from the factors and G in
    FP32 (the recompute is FP64, the tables FP32; n_sigma <= 128).  1: Gauss-Jordan elimination in

@@ -116,7 +116,8 @@ vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value) {
         return VMC_OK;
     }
     if (option == VMC_OPT_ELOC_THREADS) {
-        if (value != 128 && value != 256 && value != 512) return set_err(ctx, VMC_ERR_ARG, "128, 256 or 512 threads");
+        if (value != 128 && value != 256 && value != 384 && value != 512)
+            return set_err(ctx, VMC_ERR_ARG, "128, 256, 384 or 512 threads");
         ctx->eloc_threads = value;
         return VMC_OK;
     }
@@ -240,18 +241,25 @@ vmc_status vmc_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items,
 
 vmc_status vmc_autotune_local_energy(vmc_ctx *ctx, int n, const vmc_batch_item *items, int *threads_out) {
     if (!ctx) return VMC_ERR_ARG;
-    const int cand[3] = {128, 256, 512};
+    const int cand[4] = {128, 256, 384, 512};
     float best = 1e30f;
     int pick = ctx->eloc_threads;
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
         return set_err(ctx, VMC_ERR_CUDA, "autotune events");
-    for (int c = 0; c < 3; ++c) {
+    // one item: time the per-system launch that item's caller makes; several: the batched launch
+    auto run = [&]() -> vmc_status {
+        if (n == 1 && items)
+            return vmc_local_energy(ctx, items[0].lists, items[0].params, items[0].walkers, items[0].eps_run,
+                                    items[0].d_e_loc, items[0].d_t_res);
+        return vmc_local_energy_batch(ctx, n, items);
+    };
+    for (int c = 0; c < 4; ++c) {
         ctx->eloc_threads = cand[c];
-        vmc_status st = vmc_local_energy_batch(ctx, n, items);       // warm-up
+        vmc_status st = run();                                         // warm-up
         if (st) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
         cudaEventRecord(a, ctx->stream);
-        st = vmc_local_energy_batch(ctx, n, items);
+        st = run();
         cudaEventRecord(b, ctx->stream);
         if (st) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
         cudaError_t e = cudaEventSynchronize(b);

@@ -522,8 +522,13 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     __syncthreads();   // shared memory may be reused for the next walker
 }
 
-template <typename real>
-__global__ void __launch_bounds__(512)
+// CTA widths the local-energy kernels are built for (128, 256, 384, 512 threads), each with the
+// minimum of resident CTAs per SM that keeps it at <= 64 registers per thread, so that shared
+// memory (the walker's G rows) rather than registers bounds the CTAs per SM.
+template <int kT> struct EmB { static constexpr int v = kT >= 512 ? 2 : (kT >= 384 ? 3 : (kT >= 256 ? 4 : 8)); };
+
+template <typename real, int kT>
+__global__ void __launch_bounds__(kT, EmB<kT>::v)
 k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
                u128 *__restrict__ rates, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -532,8 +537,8 @@ k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__
 
 // Batched launch over several systems (uneven sizes).  CTAs stay resident and take walkers from
 // a global queue; the descriptors are ordered by decreasing cost so the long walkers start first.
-template <typename real>
-__global__ void __launch_bounds__(512)
+template <typename real, int kT>
+__global__ void __launch_bounds__(kT, EmB<kT>::v)
 k_local_energy_batched(const SysDesc *__restrict__ sys, int n_sys, int total, int *queue, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_item;
@@ -885,6 +890,43 @@ static WalkerArgs make_args(vmc_walkers *Wk) {
     return A;
 }
 
+template <typename real, int kT>
+static cudaError_t eloc_launch_t(const vmc_ctx *ctx, int W, size_t smem, const ListsView &L, const WalkerArgs &A,
+                                 double *e_loc, double *t_res, u128 *rates) {
+    cudaError_t e = cudaFuncSetAttribute(k_local_energy<real, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_local_energy<real, kT><<<W, kT, smem, ctx->stream>>>(L, A, e_loc, t_res, rates, ctx->d_status);
+    return e;
+}
+template <typename real>
+static cudaError_t eloc_launch(const vmc_ctx *ctx, int W, size_t smem, const ListsView &L, const WalkerArgs &A,
+                               double *e_loc, double *t_res, u128 *rates) {
+    switch (ctx->eloc_threads) {
+    case 128: return eloc_launch_t<real, 128>(ctx, W, smem, L, A, e_loc, t_res, rates);
+    case 256: return eloc_launch_t<real, 256>(ctx, W, smem, L, A, e_loc, t_res, rates);
+    case 384: return eloc_launch_t<real, 384>(ctx, W, smem, L, A, e_loc, t_res, rates);
+    default: return eloc_launch_t<real, 512>(ctx, W, smem, L, A, e_loc, t_res, rates);
+    }
+}
+template <typename real, int kT>
+static cudaError_t eloc_batched_launch_t(const vmc_ctx *ctx, int nsm, size_t se, const SysDesc *tab, int n, int total) {
+    int per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_local_energy_batched<real, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_energy_batched<real, kT>, kT, se);
+    if (e == cudaSuccess)
+        k_local_energy_batched<real, kT><<<std::max(1, per_sm) * nsm, kT, se, ctx->stream>>>(tab, n, total, ctx->d_queue,
+                                                                                            ctx->d_status);
+    return e;
+}
+template <typename real>
+static cudaError_t eloc_batched_launch(const vmc_ctx *ctx, int nsm, size_t se, const SysDesc *tab, int n, int total) {
+    switch (ctx->eloc_threads) {
+    case 128: return eloc_batched_launch_t<real, 128>(ctx, nsm, se, tab, n, total);
+    case 256: return eloc_batched_launch_t<real, 256>(ctx, nsm, se, tab, n, total);
+    case 384: return eloc_batched_launch_t<real, 384>(ctx, nsm, se, tab, n, total);
+    default: return eloc_batched_launch_t<real, 512>(ctx, nsm, se, tab, n, total);
+    }
+}
+
 vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk, double *e_loc,
                                double *t_res, u128 *rates, int n_groups) {
     const int M = Wk->M;
@@ -896,18 +938,9 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
                         eloc_queue_bytes(ctx->eloc_threads);
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
-    cudaError_t e;
-    if (Wk->precision == VMC_FP64) {
-        e = cudaFuncSetAttribute(k_local_energy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_local_energy<double><<<Wk->W, ctx->eloc_threads, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                                    ctx->d_status);
-    } else {
-        e = cudaFuncSetAttribute(k_local_energy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_local_energy<float><<<Wk->W, ctx->eloc_threads, smem, ctx->stream>>>(L->view, A, e_loc, t_res, rates,
-                                                                                   ctx->d_status);
-    }
+    cudaError_t e = Wk->precision == VMC_FP64
+                              ? eloc_launch<double>(ctx, Wk->W, smem, L->view, A, e_loc, t_res, rates)
+                              : eloc_launch<float>(ctx, Wk->W, smem, L->view, A, e_loc, t_res, rates);
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_local_energy");
@@ -1049,22 +1082,13 @@ vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *
     if (st) return st;
     if (se > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream);
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0, nsm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int threads = ctx->eloc_threads;
     const SysDesc *tab = (const SysDesc *)ctx->batch_desc;
-    if (prec == VMC_FP64) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_local_energy_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_energy_batched<double>, threads, se);
-        if (e == cudaSuccess)
-            k_local_energy_batched<double><<<std::max(1, per_sm) * nsm, threads, se, ctx->stream>>>(tab, n, total, ctx->d_queue, ctx->d_status);
-    } else {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_local_energy_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_energy_batched<float>, threads, se);
-        if (e == cudaSuccess)
-            k_local_energy_batched<float><<<std::max(1, per_sm) * nsm, threads, se, ctx->stream>>>(tab, n, total, ctx->d_queue, ctx->d_status);
-    }
+    if (e == cudaSuccess)
+        e = prec == VMC_FP64 ? eloc_batched_launch<double>(ctx, nsm, se, tab, n, total)
+                             : eloc_batched_launch<float>(ctx, nsm, se, tab, n, total);
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(ctx, e, "k_local_energy_batched");
