@@ -127,11 +127,13 @@ class Clocks:
 
 
 # ncu counters of one k_local_energy launch (mixed form, H160, eps 1e-6), per walker: DRAM bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum) and L2 bytes (lts__t_sectors.sum x 32), from the
+# (dram__bytes_read.sum + dram__bytes_write.sum), L2 bytes (lts__t_sectors.sum x 32) and warp
+# instructions (smsp__inst_executed.sum), from the
 # capture summarised in profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel
 # source with this digest only; any later change of the kernel reports traffic as null.
-ELOC_COUNTERS = {"sha256": "e7227f9b36f194ad212838d6159a9572af19dee012e7dfcfd22695677303939d",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 79589.8, "l2_bytes_per_walker": 776666.9}
+ELOC_COUNTERS = {"sha256": "9aacb2b324c341eb02b0065fad35dd67c0d63d99cb2403bb8ae6fc0958bf44a6",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 79495.2, "l2_bytes_per_walker": 789490.2,
+                 "warp_inst_per_walker": 317426.9}
 
 
 def eloc_source_digest() -> str:
@@ -553,7 +555,10 @@ def main():
     counters_ok = ("mixed" in results and eloc_source_digest() == ELOC_COUNTERS["sha256"]
                    and args.system == ELOC_COUNTERS["system"] and args.eps == ELOC_COUNTERS["eps"])
     traffic = ELOC_COUNTERS["dram_bytes_per_walker"] * args.walkers if counters_ok else None
-    l2_peak = l2_probe_gbs(torch.device("cuda", 0))
+    l2_peak = l2_probe_gbs(torch.device("cuda", torch.cuda.current_device()))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_mhz = head["clocks"].get("sm_mhz") or head["clocks"].get("sm_max_mhz") or 2070.0
+    issue_peak = 4 * props.multi_processor_count * sm_mhz * 1e6 / 1e12     # Twarp-inst/s
     l2_bytes = ELOC_COUNTERS["l2_bytes_per_walker"] * args.walkers if counters_ok else None
     scale = world
     line = {"metric": METRIC, "value": head["value"] * scale, "unit": UNIT, "n_gpus": world,
@@ -568,6 +573,14 @@ def main():
                          "peak": peak, "unit": "GB/s", "frac": head["eloc_gbs"] / peak,
                          "peak_source": peak_kind, "traffic": traffic,
                          "bytes_per_launch": head["eloc_bytes"], "launch_ms": head["eloc_ms"]},
+            "issue_roofline": {"kernel": "k_local_energy", "bound": "issue",
+                               "achieved": (ELOC_COUNTERS["warp_inst_per_walker"] * args.walkers /
+                                            (head["eloc_ms"] * 1e-3) / 1e12) if counters_ok else None,
+                               "peak": issue_peak, "unit": "Twarp-inst/s",
+                               "frac": (ELOC_COUNTERS["warp_inst_per_walker"] * args.walkers /
+                                        (head["eloc_ms"] * 1e-3) / 1e12 / issue_peak) if counters_ok else None,
+                               "peak_source": "4 schedulers x SMs x median SM clock under load, one warp "
+                                              "instruction per scheduler per clock"},
             "l2_roofline": {"kernel": "k_local_energy", "bound": "l2",
                             "achieved": (l2_bytes / (head["eloc_ms"] * 1e-3) / 1e9) if l2_bytes else None,
                             "peak": l2_peak, "unit": "GB/s",
