@@ -131,9 +131,9 @@ class Clocks:
 # instructions (smsp__inst_executed.sum), from the
 # capture summarised in profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel
 # source with this digest only; any later change of the kernel reports traffic as null.
-ELOC_COUNTERS = {"sha256": "9aacb2b324c341eb02b0065fad35dd67c0d63d99cb2403bb8ae6fc0958bf44a6",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 79495.2, "l2_bytes_per_walker": 789490.2,
-                 "warp_inst_per_walker": 317426.9}
+ELOC_COUNTERS = {"sha256": "3ce823ee3b403797eca09c76c09c007c29973370507193f84cc13bb8320df540",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80665.8, "l2_bytes_per_walker": 803356.0,
+                 "warp_inst_per_walker": 311870.6}
 
 
 def eloc_source_digest() -> str:

@@ -197,7 +197,7 @@ vmc_status vmc_local_energy(vmc_ctx *ctx, const vmc_lists *Lc, const vmc_params 
     if (st) return st;
     const int ng = L->view.n_groups;
     void *rates = nullptr;
-    st = ensure_rates(ctx, sizeof(u128) * (size_t)ng * Wk->W, &rates);
+    st = ensure_rates(ctx, sizeof(u128) * rate_store_units(Wk->W, ng), &rates);
     if (st) return st;
     st = launch_local_energy(ctx, L, Wk, e_loc, t_res, (u128 *)rates, ng);
     if (st) return st;

@@ -105,6 +105,13 @@ __host__ __device__ inline int tri_index(int p, int q, int M) {  // p < q
 }
 
 // J read from the upper triangle only
+// Rate store of one system, in 16-byte units: W x n_groups exact rate sums (u128) followed by the
+// W x n_groups per-group energy partials (FP64) that the local energy adds in a fixed order.
+inline size_t rate_store_units(size_t W, int n_groups) {
+    const size_t n = W * (size_t)n_groups;
+    return n + (n + 1) / 2;
+}
+
 __device__ __forceinline__ double jget(const double *J, int N2, int p, int q) {
     return p <= q ? J[(size_t)p * N2 + q] : J[(size_t)q * N2 + p];
 }

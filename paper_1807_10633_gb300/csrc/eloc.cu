@@ -398,8 +398,9 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     real *sGa = (real *)smraw;
     real *sGb = sGa + (size_t)geo.nv_a * lda;
     real *sE = sGb + (size_t)geo.nv_b * ldb;
-    double *eg = (double *)(((uintptr_t)(sE + 2 * M) + 7) & ~(uintptr_t)7);   // per-group energy
-    uint16_t *pos = (uint16_t *)(eg + n_groups);
+    uint16_t *pos = (uint16_t *)(sE + 2 * M);
+    // per-group energy partials: global, after the system's rate sums (written and read by this CTA)
+    double *eg = (double *)(rates + (size_t)A.W * n_groups) + (size_t)w * n_groups;
     // per warp: two queues of 64 entry codes (idx << 5 | unit lane): kinds 0/1, and kind 2
     uint32_t *wq = (uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + warp * 128;
     __shared__ u128 red_q[32];
@@ -934,8 +935,7 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    const size_t smem = esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16 +
-                        eloc_queue_bytes(ctx->eloc_threads);
+    const size_t smem = esz * (gpad + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16 + eloc_queue_bytes(ctx->eloc_threads);
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e = Wk->precision == VMC_FP64
@@ -979,8 +979,8 @@ static size_t eloc_smem_bytes(const vmc_lists *L, const vmc_walkers *Wk, int thr
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    return esz * (gpad + 2 * (size_t)M) + 8 + 8 * (size_t)L->view.n_groups + 2 * (2 * (size_t)M) + 16 +
-           eloc_queue_bytes(threads);
+    (void)L;
+    return esz * (gpad + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16 + eloc_queue_bytes(threads);
 }
 
 static size_t apply_smem_bytes(const vmc_walkers *Wk) {
@@ -1020,7 +1020,7 @@ static vmc_status prepare_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items
     for (int k = 0; k < n; ++k) {
         const vmc_batch_item &it = items[order[k]];
         rate_off[k] = rates_total;
-        rates_total += (size_t)it.walkers->W * it.lists->view.n_groups;
+        rates_total += rate_store_units(it.walkers->W, it.lists->view.n_groups);
         tot += it.walkers->W;
         se = std::max(se, eloc_smem_bytes(it.lists, it.walkers, ctx->eloc_threads));
         sa = std::max(sa, apply_smem_bytes(it.walkers));
