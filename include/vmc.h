@@ -45,7 +45,8 @@ typedef enum {
 
 typedef enum {
     VMC_FP64 = 0,          /* G, A^-1, Jastrow sums and ratios in FP64 */
-    VMC_MIXED = 1          /* G, A^-1, Jastrow sums and ratios in FP32; sums, LU, Fock sums FP64 */
+    VMC_MIXED = 1          /* G, A^-1, Jastrow and Fock sums, ratios in FP32; C_occ LU and the
+                              walker sums (energy, gradient) in FP64 */
 } vmc_precision;
 
 typedef struct vmc_ctx vmc_ctx;       /* device, stream, workspace, status word */
@@ -136,8 +137,10 @@ vmc_status vmc_walkers_sizes(int W, int M, int n_alpha, int n_beta, const vmc_li
 
 /*
  * (Re)build every walker table from occ_list (each spin block holds the walker's occupied
- * orbitals in any order) and the parameters: occ_bits, virt_list, pos, C_occ^-1 by FP64 LU with
- * partial pivoting (the one O(N^3) step of Sec. III.B), G = C C_occ^-1, S, F, e_diag.  Also
+ * orbitals in any order) and the parameters: occ_bits, virt_list, pos, C_occ^-1 (the one O(N^3)
+ * step of Sec. III.B: FP64 Gauss-Jordan with partial pivoting for VMC_FP64, FP64 LU with partial
+ * pivoting and the inverse from the factors in FP32 for VMC_MIXED; see the options below),
+ * G = C C_occ^-1 (on the tensor cores for VMC_MIXED), S, F, e_diag.  Also
  * refreshes the Jastrow constants stored with the lists for these parameters.  rng_counter is
  * left as is.  This is the periodic recompute (e.g. every 64 moves, and after every parameter
  * update).  Singular blocks latch VMC_ERR_SINGULAR.
@@ -147,8 +150,8 @@ vmc_status vmc_walkers_init(vmc_ctx *ctx, vmc_lists *lists, const vmc_params *pa
 
 /*
  * After a parameter update: refresh the parameter-dependent tables only (Jastrow constants of
- * the lists, C_occ^-1 by FP64 LU, G, S).  F and e_diag depend on the occupations alone and are
- * kept.  Same errors as vmc_walkers_init.
+ * the lists, C_occ^-1 as in vmc_walkers_init, G, S; the mixed form also recomputes F).  e_diag
+ * depends on the occupations alone and is kept.  Same errors as vmc_walkers_init.
  */
 vmc_status vmc_walkers_refresh(vmc_ctx *ctx, vmc_lists *lists, const vmc_params *params,
                                vmc_walkers *walkers);
