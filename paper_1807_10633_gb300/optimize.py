@@ -99,6 +99,9 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
+    ap.add_argument("--alpha0", type=float, default=0.001, help="step size of the first --warm iterations")
+    ap.add_argument("--alpha1", type=float, default=0.01, help="step size afterwards")
+    ap.add_argument("--warm", type=int, default=5)
     args = ap.parse_args()
     sys_ = S.named_system(args.system)
     prm = S.make_params(sys_, seed=args.seed)
@@ -108,6 +111,7 @@ def main():
     vmc.Batch([eng]).autotune()
     t0 = time.perf_counter()
     its = optimize(eng, args.iters, args.sweeps, seed=args.seed, burn_in=args.burn_in, n_elec=sys_.n_elec,
+                   alpha0=args.alpha0, alpha1=args.alpha1, warm=args.warm,
                    callback=lambda it: print(json.dumps(it.__dict__), flush=True))
     print(json.dumps({"system": args.system, "walkers": args.walkers, "sweeps": args.sweeps,
                       "form": args.form, "eps": args.eps, "wall_s": time.perf_counter() - t0,
