@@ -75,6 +75,59 @@ def test_direct_ratios_equal_table_ratios():
         np.testing.assert_allclose(e1, e2, rtol=1e-12)
 
 
+# --- in-place replacement convention and the a <-> b identity (Sec. III.B, Eq. R) -------
+def test_double_contribution_is_inplace_minor_and_symmetric_in_ab():
+    # The oracle's H_nm (explicit canonical phase) times psi(m)/psi(n) equals, for every double,
+    # the in-place form <ab||ij> x (2x2 minor of G = C C_occ^-1) x Jastrow ratio with no sign
+    # bookkeeping, and that form is unchanged when a and b are swapped (both factors flip sign).
+    sys = _h6()
+    prm = S.make_params(sys, seed=21, j_scale=0.1, c_noise=0.2)
+    orc = Oracle(sys, prm)
+    M, e = sys.M, sys.eri
+    dets = brute.all_dets(sys.M, sys.n_alpha, sys.n_beta)
+    n_all = brute.occupations(dets, sys.M)
+    Jm = np.triu(prm.J)
+
+    def logj(n):
+        x = n.astype(float)
+        return x @ Jm @ x                   # upper triangle incl. diagonal: sum_{p<=q} J_pq n_p n_q
+
+    rng = np.random.default_rng(3)
+    checked = 0
+    for d in rng.choice(len(n_all), 12, replace=False):
+        n = n_all[d]
+        _, _, moves = orc.local_energy(n, 0.0)
+        G, col = [], []
+        for sg, C in ((0, prm.C_alpha), (1, prm.C_beta)):
+            occ = np.flatnonzero(n[sg * M:(sg + 1) * M])
+            G.append(C @ np.linalg.inv(C[occ]))
+            col.append({int(k): c for c, k in enumerate(occ)})
+        for mv in moves[moves["kind"] == 2]:
+            i, j, a, b = (int(mv[f]) for f in ("i", "j", "a", "b"))
+            si, sj = i // M, j // M
+            pi, pj, pa, pb = i % M, j % M, a % M, b % M
+            m = n.copy(); m[[i, j]] = 0; m[[a, b]] = 1
+            jr = math.exp(logj(m) - logj(n))
+
+            def inplace(pa, pb):
+                if si == sj:
+                    g, c = G[si], col[si]
+                    v = e[pa, pi, pb, pj] - e[pa, pj, pb, pi]
+                    minor = g[pa, c[pi]] * g[pb, c[pj]] - g[pa, c[pj]] * g[pb, c[pi]]
+                else:
+                    v = e[pa, pi, pb, pj]
+                    minor = G[0][pa, col[0][pi]] * G[1][pb, col[1][pj]]
+                return v * minor * jr
+
+            ref = mv["h"] * mv["ratio"]
+            got = inplace(pa, pb)
+            assert abs(got - ref) <= 1e-10 * max(1.0, abs(ref)), (i, j, a, b)
+            if si == sj:
+                assert abs(inplace(pb, pa) - got) <= 1e-12 * max(1.0, abs(got))
+            checked += 1
+    assert checked > 100
+
+
 # --- energy expectation and the variational bound (Eq. vmc) ------------------------------
 def test_energy_is_rho_weighted_mean_and_variational(hub10):
     sys, prm, dets, H, n, psi = hub10
