@@ -491,9 +491,17 @@ def cpu_baseline(args, sys_, prm, occ, sample: int):
     t = time.perf_counter()
     orc.sweep(n, args.eps, args.seed, ctr, n_threads=nt)
     dt = time.perf_counter() - t
+    # one thread on a few of the same walkers (the oracle's single-core rate)
+    s1 = max(1, min(sample, 4))
+    n1 = np.ascontiguousarray(oracle.occ_lists_to_n(occ[:s1], sys_.M, sys_.n_alpha))
+    t = time.perf_counter()
+    orc.sweep(n1, args.eps, args.seed, np.zeros(s1, dtype=np.uint64), n_threads=1)
+    dt1 = time.perf_counter() - t
     return dict(value=sample / dt, unit=UNIT, cores=nt, kind="oracle",
                 sample=f"{sample} walkers x 1 CTMC step (E_L + choice + move) of the same workload, "
-                       f"FP64 oracle, OpenMP over walkers, {dt:.1f} s")
+                       f"FP64 oracle, OpenMP over walkers, {dt:.1f} s",
+                single_thread={"value": s1 / dt1, "unit": UNIT, "cores": 1,
+                               "sample": f"{s1} walkers x 1 CTMC step on one thread, {dt1:.1f} s"})
 
 
 def main():
