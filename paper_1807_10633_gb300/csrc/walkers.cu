@@ -345,26 +345,107 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
         }
         __syncthreads();
     }
+    // ---- Y <- U'^-1 D^-1 L^-1 Y by blocked substitution: per block of kSB pivot rows every warp
+    //      solves the block for its lanes' columns in registers (redundantly, a few FMAs), then
+    //      updates its share of the other rows with all kSB pivot rows at once; one barrier per
+    //      block.  The finished block rows are stored after the barrier (no warp reads them again).
     const int nwarp = nt >> 5;
-    for (int k = 0; k < n - 1; ++k) {             // forward: L (unit diagonal)
-        for (int r = k + 1 + warp; r < n; r += nwarp) {
-            const float l = LUf[r * ld + k];
-            for (int c = lane; c < n; c += 32) Y[r * ld + c] -= l * Y[k * ld + c];
+    constexpr int kSB = 4, kCL = (VMC_MAX_M / 2 + 31) / 32;   // pivot rows per block, columns per lane
+    for (int k0 = 0; k0 < n; k0 += kSB) {          // forward: L (unit diagonal)
+        const int kb = min(kSB, n - k0);
+        float yh[kSB][kCL];
+#pragma unroll
+        for (int t = 0; t < kSB; ++t)
+#pragma unroll
+            for (int i = 0; i < kCL; ++i) {
+                const int c = lane + 32 * i;
+                yh[t][i] = (t < kb && c < n) ? Y[(k0 + t) * ld + c] : 0.0f;
+            }
+#pragma unroll
+        for (int t = 1; t < kSB; ++t)
+#pragma unroll
+            for (int q = 0; q < kSB - 1; ++q)
+                if (q < t && t < kb) {
+                    const float l = LUf[(k0 + t) * ld + k0 + q];
+#pragma unroll
+                    for (int i = 0; i < kCL; ++i) yh[t][i] -= l * yh[q][i];
+                }
+        for (int r = k0 + kb + warp; r < n; r += nwarp) {
+            float l[kSB];
+#pragma unroll
+            for (int t = 0; t < kSB; ++t) l[t] = t < kb ? LUf[r * ld + k0 + t] : 0.0f;
+#pragma unroll
+            for (int i = 0; i < kCL; ++i) {
+                const int c = lane + 32 * i;
+                if (c < n) {
+                    float v = Y[r * ld + c];
+#pragma unroll
+                    for (int t = 0; t < kSB; ++t) v -= l[t] * yh[t][i];
+                    Y[r * ld + c] = v;
+                }
+            }
         }
         __syncthreads();
+#pragma unroll
+        for (int t = 1; t < kSB; ++t)
+            if (t < kb && warp == (t - 1) % nwarp)
+#pragma unroll
+                for (int i = 0; i < kCL; ++i) {
+                    const int c = lane + 32 * i;
+                    if (c < n) Y[(k0 + t) * ld + c] = yh[t][i];
+                }
     }
+    __syncthreads();
     for (int r = warp; r < n; r += nwarp) {       // D^-1
         const float d = LUf[r * ld + r];
         for (int c = lane; c < n; c += 32) Y[r * ld + c] *= d;
     }
     __syncthreads();
-    for (int k = n - 1; k > 0; --k) {             // backward: U' (unit diagonal)
-        for (int r = warp; r < k; r += nwarp) {
-            const float u = LUf[r * ld + k];
-            for (int c = lane; c < n; c += 32) Y[r * ld + c] -= u * Y[k * ld + c];
+    for (int k1 = n - 1; k1 >= 0; k1 -= kSB) {     // backward: U' (unit diagonal), blocks from the bottom
+        const int kb = min(kSB, k1 + 1), p0 = k1 - kb + 1;   // block rows p0 .. k1
+        float yh[kSB][kCL];
+#pragma unroll
+        for (int t = 0; t < kSB; ++t)
+#pragma unroll
+            for (int i = 0; i < kCL; ++i) {
+                const int c = lane + 32 * i;
+                yh[t][i] = (t < kb && c < n) ? Y[(p0 + t) * ld + c] : 0.0f;
+            }
+#pragma unroll
+        for (int t = kSB - 2; t >= 0; --t)
+#pragma unroll
+            for (int q = 1; q < kSB; ++q)
+                if (q > t && q < kb) {
+                    const float u = LUf[(p0 + t) * ld + p0 + q];
+#pragma unroll
+                    for (int i = 0; i < kCL; ++i) yh[t][i] -= u * yh[q][i];
+                }
+        for (int r = warp; r < p0; r += nwarp) {
+            float u[kSB];
+#pragma unroll
+            for (int t = 0; t < kSB; ++t) u[t] = t < kb ? LUf[r * ld + p0 + t] : 0.0f;
+#pragma unroll
+            for (int i = 0; i < kCL; ++i) {
+                const int c = lane + 32 * i;
+                if (c < n) {
+                    float v = Y[r * ld + c];
+#pragma unroll
+                    for (int t = 0; t < kSB; ++t) v -= u[t] * yh[t][i];
+                    Y[r * ld + c] = v;
+                }
+            }
         }
         __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kSB - 1; ++t)
+            if (t < kb - 1 && warp == t % nwarp)
+#pragma unroll
+                for (int i = 0; i < kCL; ++i) {
+                    const int c = lane + 32 * i;
+                    if (c < n) Y[(p0 + t) * ld + c] = yh[t][i];
+                }
     }
+    __syncthreads();
     // Y = B^-1 = (C_occ^T)^-1 = AinvT
     const size_t gofs = (size_t)w * ((size_t)(M - na) * na + (size_t)(M - nb) * nb) +
                         (sg ? (size_t)(M - na) * na : 0);
