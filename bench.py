@@ -508,7 +508,9 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if world > 1:
+    if args.impl == "reference" and rank != 0:
+        return                     # the CPU reference arm runs on rank 0 alone, with no process group
+    if world > 1 and args.impl != "reference":
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -532,8 +534,6 @@ def main():
     s_cnt = singles_counts(sys_, args.eps)
 
     if args.impl == "reference":
-        if rank != 0:
-            return
         sample = args.cpu_sample or cpu_sample_default()
         vals = []
         for _ in range(args.steps):

@@ -1,0 +1,41 @@
+"""The reference arm of bench.py (the FP64 oracle on the host cores, a bounded sample) prints one
+JSON line with the benchmark's keys, once, from rank 0 only; CPU only."""
+import json
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parents[1]
+ARGS = ["--impl", "reference", "--system", "H20", "--walkers", "64", "--cpu-sample", "8",
+        "--steps", "2", "--warmup", "3"]
+KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+
+
+def _lines(out: str):
+    return [json.loads(x) for x in out.splitlines() if x.startswith("{")]
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    r = subprocess.run([sys.executable, str(ROOT / "bench.py"), *ARGS], cwd=ROOT, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    (line,) = _lines(r.stdout)
+    assert KEYS <= set(line)
+    assert line["impl"] == "reference" and line["higher_is_better"] is True and line["steps"] == 2
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert "workload" in line["config"]
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29517", str(ROOT / "bench.py"),
+                        "--gpus", "2", *ARGS], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    (line,) = _lines(r.stdout)
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
