@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven batched workload")
     ap.add_argument("--g-cuda-cores", action="store_true", help="form G on CUDA cores instead of tcgen05")
+    ap.add_argument("--grad-j-int", action="store_true",
+                    help="sum the Jastrow gradient block on the integer pipe instead of tcgen05")
     ap.add_argument("--batch-walkers", type=int, default=2048)
     ap.add_argument("--eps-sweep", default="", help="comma-separated eps values: run the eps / size study "
                     "(cost per 1000 samples of H chains) instead of the benchmark")
@@ -187,6 +189,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=dev.index, stream=stream)
     if args.g_cuda_cores:
         vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, 0)
+    if args.grad_j_int:
+        vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_GRAD_J_TENSOR_CORES, 0)
     if gj32:   # mixed tables, C_occ inverted by FP32 Gauss-Jordan at every refresh
         vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_MIXED_REFRESH_GJ32, 1)
         eng.refresh()

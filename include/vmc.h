@@ -297,11 +297,16 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
    4x faster on GB300, whose FP64 rate is 1/64 of its FP32 rate.
    VMC_OPT_REFRESH_SMEM (default 0): 1 replaces the register Gauss-Jordan kernels by the
    shared-memory kernels (mixed: the FP64 LU above; FP64: Gauss-Jordan with row exchanges,
-   n_sigma <= 118); the FP64 form's default is the register Gauss-Jordan in FP64. */
+   n_sigma <= 118); the FP64 form's default is the register Gauss-Jordan in FP64.
+   VMC_OPT_GRAD_J_TENSOR_CORES (default 1): the Jastrow block of vmc_grad_logpsi and
+   vmc_accumulate_gradient, sum_w c_w n_p n_q over walkers, runs as tcgen05 TF32 products of the
+   0/1 occupation matrix with the eight base-256 digits of each 64-bit fixed-point weight (exact;
+   0: the same fixed-point sums on the integer pipe).  Both give bit-identical results. */
 #define VMC_OPT_G_TENSOR_CORES 1
 #define VMC_OPT_ELOC_THREADS 2
 #define VMC_OPT_REFRESH_SMEM 3
 #define VMC_OPT_MIXED_REFRESH_GJ32 4
+#define VMC_OPT_GRAD_J_TENSOR_CORES 5
 vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value);
 
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */

@@ -129,6 +129,10 @@ vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value) {
         ctx->mixed_gj32 = value ? 1 : 0;
         return VMC_OK;
     }
+    if (option == VMC_OPT_GRAD_J_TENSOR_CORES) {
+        ctx->grad_j_tc = value ? 1 : 0;
+        return VMC_OK;
+    }
     return set_err(ctx, VMC_ERR_ARG, "unknown option");
 }
 

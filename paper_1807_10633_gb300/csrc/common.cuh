@@ -45,6 +45,7 @@ struct vmc_ctx {
     int g_tensor_cores = 1;        // mixed refresh: G on tcgen05 (1) or CUDA cores (0)
     int refresh_smem = 0;          // refresh: register Gauss-Jordan (0) or shared-memory LU/GJ (1)
     int mixed_gj32 = 0;            // mixed refresh: FP64 LU of C_occ (0) or FP32 register Gauss-Jordan (1)
+    int grad_j_tc = 1;             // Jastrow walker sums: tcgen05 digit products (1) or integer pipe (0)
 };
 
 // Plain-pointer view of the device lists, passed to kernels by value.
@@ -211,6 +212,9 @@ vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);
 size_t g_umma_smem(int M, int na, int nb);
+vmc_status launch_grad_J_umma(vmc_ctx *ctx, int W, int M, const uint32_t *bits, const long long *cq, int mode,
+                              long long *part, int chunk, int n_chunks);
+void grad_j_umma_chunks(int W, int M, int nsm, int *chunk, int *n_chunks);
 vmc_status launch_grad(vmc_ctx *ctx, const vmc_walkers *Wk, const double *w, double *dJ,
                        double *dCa, double *dCb);
 vmc_status launch_accumulate(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t, const double *e,

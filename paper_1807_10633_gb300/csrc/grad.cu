@@ -291,7 +291,16 @@ static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t
                             double *const out0[3], double *const out1[3], double *sums) {
     const int W = Wk->W, M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta, N2 = 2 * M;
     const int T = (N2 + 31) / 32, ntile = T * (T + 1) / 2;
-    const int cj = (W + kChunkJ - 1) / kChunkJ, cc = (W + kChunkC - 1) / kChunkC;
+    const int cc = (W + kChunkC - 1) / kChunkC;
+    const bool jtc = ctx->grad_j_tc != 0 && out0[0] != nullptr;
+    int cj = (W + kChunkJ - 1) / kChunkJ, chunk_j = kChunkJ;
+    if (jtc) {
+        int dev = 0, nsm = 0;
+        cudaError_t err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (err != cudaSuccess) return cuda_check(ctx, err, "device attributes");
+        grad_j_umma_chunks(W, M, nsm, &chunk_j, &cj);
+    }
     const int nmax = na > nb ? na : nb, nout = mode + 1;
     if (nmax > 128) return set_err(ctx, VMC_ERR_ARG, "n_sigma > 128 is not supported by the gradient kernel");
     const size_t head = 256 + sizeof(long long) * 2 * (size_t)W;
@@ -305,10 +314,16 @@ static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t
     k_weight_prep<<<1, 1024, 0, ctx->stream>>>(W, t, e, mode, cq, sexp, sums);
     ctx->launches += 1;
     if (out0[0]) {
-        k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, cq, mode, (long long *)part);
+        if (jtc) {
+            st = launch_grad_J_umma(ctx, W, M, Wk->occ_bits, cq, mode, (long long *)part, chunk_j, cj);
+            if (st) return st;     // (the launch is counted there)
+        } else {
+            k_grad_J<<<dim3(ntile, cj), 256, 0, ctx->stream>>>(W, M, Wk->occ_bits, cq, mode, (long long *)part);
+            ctx->launches += 1;
+        }
         k_reduce_J<<<(N2 * N2 + 255) / 256, 256, 0, ctx->stream>>>(M, cj, (const long long *)part, sexp, out0[0],
                                                                    mode ? out1[0] : nullptr);
-        ctx->launches += 2;
+        ctx->launches += 1;
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return cuda_check(ctx, err, "k_grad_J");
     }

@@ -269,7 +269,242 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Jastrow block of the walker sums (Sec. III.B: O_pq = n_p n_q) on the tensor cores, exactly.
+//
+// part[o][c][p][q] = sum over the walkers w of chunk c of cq_o[w] n_w[p] n_w[q]  (p <= q),
+// the same 64-bit fixed-point sums as the integer kernel.  The weights are split into eight
+// balanced base-256 digits, cq = sum_l d_l 256^l with d_l in [-128, 128), and for every digit
+// D_l[p][j] = sum_w n_w[p] (d_l,w n_w[q_j]) is a product of a 0/1 matrix and a small-integer
+// matrix: TF32 holds both operands exactly and the FP32 accumulation is exact while every
+// partial sum stays below 2^24 (|D_l| <= 128 x walkers per chunk <= 2^23).  The epilogue forms
+// sum_l D_l 256^l in 64-bit integers with wrapping arithmetic; the chunk's true sum is below
+// 2^62 in magnitude, so the wrapped result is exact.
+//
+// CTA = (tile, walker chunk).  Tile = 128 spin orbitals p (MMA rows) x 32 spin orbitals q, with
+// every (p, q <= ...) block that holds some p <= q.  MMA columns j = 256 o + 32 l + q' (weight
+// set o, digit l, q = 32 Q + q'); one or two N = 256 accumulators in tensor memory.  Walkers are
+// staged 32 at a time (the K dimension) into double-buffered K-major core-matrix tiles.
+constexpr int kJB = 32;                 // walkers per K block
+constexpr int kJDig = 8;                // base-256 digits of a 64-bit weight
+constexpr int kJMaxChunk = 65536;       // walkers per chunk: 128 x 65536 = 2^23 < 2^24
+constexpr uint32_t kJA = 128 * kJB * 4; // bytes of the A tile (128 rows)
+constexpr uint32_t kJBset = 256 * kJB * 4; // bytes of one weight set's B tile (256 rows)
+
+__host__ __device__ inline int grad_j_tiles(int N2) {
+    const int nP = (N2 + 127) / 128, nQ = (N2 + 31) / 32;
+    int t = 0;
+    for (int P = 0; P < nP; ++P) t += nQ - 4 * P;
+    return t;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const long long *__restrict__ cq,
+              int mode, long long *__restrict__ part, unsigned *status) {
+    const int N2 = 2 * M, nw = (M + 31) / 32, nW2 = 2 * nw;
+    const int nQ = (N2 + 31) / 32;
+    int t = blockIdx.x, P = 0;
+    while (t >= nQ - 4 * P) { t -= nQ - 4 * P; ++P; }
+    const int Q = 4 * P + t;                       // tiles with 32 Q + 31 >= 128 P
+    const int n_sets = mode ? 2 : 1;
+    const int c = blockIdx.y, n_chunks = gridDim.y;
+    const int w_begin = c * chunk, w_end = min(W, w_begin + chunk);
+    const int nblk = w_end > w_begin ? (w_end - w_begin + kJB - 1) / kJB : 0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)sm + 1023) & ~(uintptr_t)1023);
+    const uint32_t buf_bytes = kJA + (uint32_t)n_sets * kJBset;
+    uint32_t *s_bits = (uint32_t *)(base + 2 * buf_bytes);          // [kJB][2 nw]
+    float *s_dig = (float *)(s_bits + kJB * 16);                      // [set][digit][kJB]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint32_t ncols = mode ? 512u : 256u;
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0u, pending = 0u;   // bit b: mbarrier b's phase parity / a commit not yet awaited
+
+    // occupation bit of spin orbital p (< N2) in the staged words of block walker wl
+    auto bit = [&](int wl, int p) -> uint32_t {
+        const int s = p >= M, k = p - s * M;
+        return (s_bits[wl * nW2 + s * nw + (k >> 5)] >> (k & 31)) & 1u;
+    };
+
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int buf = blk & 1, w0 = w_begin + blk * kJB;
+        // stage the block's occupation words and weight digits
+        for (int i = tid; i < kJB * nW2; i += kThreads) {
+            const int wl = i / nW2, k = i - wl * nW2;
+            s_bits[i] = w0 + wl < w_end ? bits[(size_t)(w0 + wl) * nW2 + k] : 0u;
+        }
+        if (tid < kJB * n_sets) {
+            const int wl = tid & (kJB - 1), o = tid / kJB;
+            long long x = w0 + wl < w_end ? cq[(size_t)o * W + w0 + wl] : 0;
+#pragma unroll
+            for (int l = 0; l < kJDig; ++l) {
+                const int d = (int)(signed char)(x & 0xFF);
+                s_dig[(o * kJDig + l) * kJB + wl] = (float)d;
+                x = (x - d) >> 8;
+            }
+        }
+        if ((pending >> buf) & 1u) {   // the MMAs that last read this buffer (block blk - 2)
+            if (!mbar_wait(&mbar[buf], (phase >> buf) & 1u)) abort_flag = 1;
+            phase ^= 1u << buf;
+            pending &= ~(1u << buf);
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        unsigned char *At = base + (size_t)buf * buf_bytes, *Bt = At + kJA;
+        // A[p][w] = n_w[128 P + p]: 16-byte chunk e = 4 walkers of one row (core-matrix order)
+        for (int e = tid; e < 128 * kJB / 4; e += kThreads) {
+            const int r8 = e & 7, cm = e >> 3, kc = cm % (kJB / 4), rg = cm / (kJB / 4);
+            const int p = P * 128 + rg * 8 + r8;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < N2) {
+                v.x = (float)bit(kc * 4 + 0, p); v.y = (float)bit(kc * 4 + 1, p);
+                v.z = (float)bit(kc * 4 + 2, p); v.w = (float)bit(kc * 4 + 3, p);
+            }
+            *(float4 *)(At + (uint32_t)e * 16) = v;
+        }
+        // B[256 o + 32 l + q'][w] = d_l,o[w] n_w[32 Q + q']: lane = q', warp = 4-walker group
+        {
+            const int q = Q * 32 + lane, kc = warp;
+            uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+            if (q < N2) {
+                m0 = 0u - bit(kc * 4 + 0, q); m1 = 0u - bit(kc * 4 + 1, q);
+                m2 = 0u - bit(kc * 4 + 2, q); m3 = 0u - bit(kc * 4 + 3, q);
+            }
+            for (int o = 0; o < n_sets; ++o) {
+                unsigned char *Bo = Bt + (size_t)o * kJBset;
+#pragma unroll
+                for (int l = 0; l < kJDig; ++l) {
+                    const uint4 d = *(const uint4 *)(s_dig + (o * kJDig + l) * kJB + kc * 4);
+                    const int row = l * 32 + lane;
+                    *(uint4 *)(Bo + core_off(row, kc * 4, kJB / 4)) = make_uint4(d.x & m0, d.y & m1, d.z & m2, d.w & m3);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t idesc = make_idesc(128, 256);
+            const uint32_t lbo = 128, sbo = (kJB / 4) * 128;
+            const uint32_t a0 = smem_u32(At), b0 = smem_u32(Bt);
+            for (int ks = 0; ks < kJB / 8; ++ks) {
+                const uint32_t koff = (uint32_t)ks * 256;
+                const uint64_t da = make_desc(a0 + koff, lbo, sbo);
+                for (int o = 0; o < n_sets; ++o) {
+                    const uint64_t db = make_desc(b0 + (uint32_t)o * kJBset + koff, lbo, sbo);
+                    const uint32_t acc = tmem + (uint32_t)(o * 256), accum = (blk > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(acc), "l"(da), "l"(db), "r"(idesc), "r"(accum));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&mbar[buf])));
+        }
+        pending |= 1u << buf;
+    }
+    for (int b = 0; b < 2; ++b)
+        if ((pending >> b) & 1u) {
+            if (!mbar_wait(&mbar[b], (phase >> b) & 1u)) abort_flag = 1;
+            phase ^= 1u << b;
+        }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (!abort_flag) {
+        // warps 4g..4g+3 drain (set, q half) pairs k = g, g + 2, ...: lane = row of its sub-partition
+        const int wq = warp & 3, g = warp >> 2, p = P * 128 + wq * 32 + lane;
+        for (int k = g; k < 2 * n_sets; k += 2) {
+            const int o = k >> 1, h = k & 1;
+            uint64_t acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            if (nblk > 0) {
+#pragma unroll 1
+                for (int l = 0; l < kJDig; ++l) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(o * 256 + l * 32 + h * 16);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[j] += (uint64_t)(long long)__float2ll_rn(__uint_as_float(r[j])) << (8 * l);
+                }
+            }
+            long long *dst = part + ((size_t)o * n_chunks + c) * (size_t)N2 * N2;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int q = Q * 32 + h * 16 + j;
+                if (p < N2 && q < N2 && p <= q) dst[(size_t)p * N2 + q] = (long long)acc[j];
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(status, VMC_DEV_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    }
+}
+
 }  // namespace
+
+// Walker chunking of the tensor-core Jastrow sums: about one CTA per SM over all tiles, chunks a
+// multiple of the K block and at most kJMaxChunk walkers (the exactness bound).
+void grad_j_umma_chunks(int W, int M, int nsm, int *chunk, int *n_chunks) {
+    const int T = grad_j_tiles(2 * M);
+    int nc = nsm / T;
+    if (nc < 1) nc = 1;
+    const int nblk = (W + kJB - 1) / kJB;
+    if (nc > nblk) nc = nblk;
+    int ch = ((W + nc - 1) / nc + kJB - 1) / kJB * kJB;
+    if (ch > kJMaxChunk) ch = kJMaxChunk;
+    if (ch < kJB) ch = kJB;
+    *chunk = ch;
+    *n_chunks = (W + ch - 1) / ch;
+}
+
+size_t grad_j_umma_smem(int mode) {
+    const size_t buf = kJA + (size_t)(mode ? 2 : 1) * kJBset;
+    return 1024 + 2 * buf + sizeof(uint32_t) * kJB * 16 + sizeof(float) * 2 * kJDig * kJB;
+}
+
+vmc_status launch_grad_J_umma(vmc_ctx *ctx, int W, int M, const uint32_t *bits, const long long *cq, int mode,
+                              long long *part, int chunk, int n_chunks) {
+    if (M < 1 || M > 256 || chunk < kJB || chunk > kJMaxChunk || chunk % kJB) return VMC_ERR_ARG;
+    const size_t smem = grad_j_umma_smem(mode);
+    cudaError_t e = cudaFuncSetAttribute(k_grad_J_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        k_grad_J_umma<<<dim3(grad_j_tiles(2 * M), n_chunks), kThreads, smem, ctx->stream>>>(
+            W, M, chunk, bits, cq, mode, part, ctx->d_status);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_check(ctx, e, "k_grad_J_umma");
+}
 
 // Shared memory of the persistent G kernel, or 0 when the shapes are outside its range.
 size_t g_umma_smem(int M, int na, int nb) {

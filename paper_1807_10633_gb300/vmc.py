@@ -17,6 +17,7 @@ from .build import LIB
 
 VMC_FP64, VMC_MIXED = 0, 1
 VMC_OPT_G_TENSOR_CORES, VMC_OPT_ELOC_THREADS, VMC_OPT_REFRESH_SMEM, VMC_OPT_MIXED_REFRESH_GJ32 = 1, 2, 3, 4
+VMC_OPT_GRAD_J_TENSOR_CORES = 5
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_SINGULAR", 5: "ERR_TIMEOUT",
            6: "ERR_OVERFLOW", 7: "ERR_NOMOVE"}
 

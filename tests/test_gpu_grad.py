@@ -37,6 +37,35 @@ def test_vjp_matches_oracle_sum(vmc, precision, tol):
     eng.close()
 
 
+@pytest.mark.parametrize("name,W", [("H6", 1), ("hubbard10", 33), ("H20", 777), ("H100", 2049), ("H160", 4099)])
+def test_jastrow_sums_tensor_cores_equal_integer_pipe(vmc, name, W):
+    """The tcgen05 digit-product path and the integer-pipe path give bit-identical Jastrow sums,
+    for the VJP and for the accumulated (t, t E_L) pair: spin-orbital counts inside one tile and
+    across several (ragged last tile), ragged walker counts, weights over nine decades."""
+    sys_, prm, occ = make_case(name, W)
+    eng = vmc.Engine(sys_, prm, occ, eps=1e-6, precision=vmc.VMC_MIXED)
+    try:
+        rng = np.random.default_rng(11)
+        w = torch.tensor(rng.normal(size=W) * 10.0 ** rng.integers(-4, 5, size=W), device="cuda")
+        t = torch.tensor(np.abs(rng.normal(size=W)) + 0.1, device="cuda")
+        e = torch.tensor(rng.normal(size=W) * 50.0, device="cuda")
+        res = []
+        for tc in (1, 0):
+            vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_GRAD_J_TENSOR_CORES, tc)
+            dJ, _, _ = eng.grad_logpsi(w)
+            AO = torch.zeros(eng.n_params, dtype=torch.float64, device="cuda")
+            AEO = torch.zeros_like(AO)
+            sums = torch.zeros(2, dtype=torch.float64, device="cuda")
+            vmc.vmc_accumulate_gradient(eng.ctx, eng.walkers.struct(), t, e, eng.split(AO), eng.split(AEO), sums)
+            eng.sync()
+            res.append((dJ.cpu().numpy(), AO.cpu().numpy(), AEO.cpu().numpy()))
+        for a, b in zip(*res):
+            assert np.array_equal(a, b)
+        assert np.abs(res[0][0]).max() > 0 and np.abs(res[0][2]).max() > 0
+    finally:
+        eng.close()
+
+
 def test_amsgrad_matches_oracle(vmc):
     rng = np.random.default_rng(6)
     n = 100_003
