@@ -228,18 +228,41 @@ k_grad_C(int W, int M, int na, int nb, const uint16_t *__restrict__ pos, const r
     }
 }
 
-__global__ void k_reduce_C(int M, int na, int nb, int n_chunks, int n_out, const double *__restrict__ part,
-                           double *__restrict__ dCa, double *__restrict__ dCb, double *__restrict__ dCa2,
-                           double *__restrict__ dCb2) {
+// Sum of the dC partials over walker chunks.  CTA = 32 consecutive outputs (lanes, coalesced) x 8
+// warps; warp v adds chunks v, v + 8, ... into four running sums (more loads in flight), then the
+// eight warp sums are added in warp order: a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(256)
+k_reduce_C(int M, int na, int nb, int n_chunks, int n_out, const double *__restrict__ part,
+           double *__restrict__ dCa, double *__restrict__ dCb, double *__restrict__ dCa2, double *__restrict__ dCb2) {
+    __shared__ double red[8][33];
     const int nmax = na > nb ? na : nb;
-    const int tot = M * na + M * nb;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_out * tot; t += gridDim.x * blockDim.x) {
-        const int o = t / tot, r = t - o * tot;
-        const int s = r >= M * na;
-        const int u = s ? r - M * na : r;
+    const int tot = M * na + M * nb, total = n_out * tot;
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    const int o = t / tot, r = t - o * tot;
+    const int s = r >= M * na;
+    const int u = s ? r - M * na : r;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (t < total) {
+        const size_t mn = (size_t)M * nmax, stride = 2 * mn;
+        const double *src = part + ((size_t)o * n_chunks * 2 + s) * mn + u;
+        int c = v;
+        for (; c + 24 < n_chunks; c += 32) {
+            acc[0] += src[(size_t)c * stride];
+            acc[1] += src[(size_t)(c + 8) * stride];
+            acc[2] += src[(size_t)(c + 16) * stride];
+            acc[3] += src[(size_t)(c + 24) * stride];
+        }
+        if (c < n_chunks) acc[0] += src[(size_t)c * stride];            // at most three left
+        if (c + 8 < n_chunks) acc[1] += src[(size_t)(c + 8) * stride];
+        if (c + 16 < n_chunks) acc[2] += src[(size_t)(c + 16) * stride];
+    }
+    red[v][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    __syncthreads();
+    if (v == 0 && t < total) {
         double sum = 0.0;
-        for (int c = 0; c < n_chunks; ++c)
-            sum += part[(((size_t)o * n_chunks + c) * 2 + s) * (size_t)M * nmax + u];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += red[k][lane];
         double *dst = o == 0 ? (s ? dCb : dCa) : (s ? dCb2 : dCa2);
         dst[u] += sum;
     }
@@ -338,7 +361,7 @@ static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t
             k_grad_C<float, float><<<grid, threads, 0, ctx->stream>>>(W, M, na, nb, Wk->pos, (const float *)Wk->AinvT,
                                                                       t, e, mode, (double *)part);
         const int tot = nout * (M * na + M * nb);
-        k_reduce_C<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, cc, nout, (const double *)part, out0[1],
+        k_reduce_C<<<(tot + 31) / 32, 256, 0, ctx->stream>>>(M, na, nb, cc, nout, (const double *)part, out0[1],
                                                                out0[2], mode ? out1[1] : nullptr, mode ? out1[2] : nullptr);
         ctx->launches += 2;
         cudaError_t err = cudaGetLastError();

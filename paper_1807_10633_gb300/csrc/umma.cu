@@ -314,8 +314,8 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *base = (unsigned char *)(((uintptr_t)sm + 1023) & ~(uintptr_t)1023);
     const uint32_t buf_bytes = kJA + (uint32_t)n_sets * kJBset;
-    uint32_t *s_bits = (uint32_t *)(base + 2 * buf_bytes);          // [kJB][2 nw]
-    float *s_dig = (float *)(s_bits + kJB * 16);                      // [set][digit][kJB]
+    uint32_t *s_bits = (uint32_t *)(base + 2 * buf_bytes);          // [2][kJB][2 nw]
+    float *s_dig = (float *)(s_bits + 2 * kJB * 16);                  // [2][set][digit][kJB]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -337,36 +337,59 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
     const uint32_t tmem = tmem_base;
     uint32_t phase = 0u, pending = 0u;   // bit b: mbarrier b's phase parity / a commit not yet awaited
 
-    // occupation bit of spin orbital p (< N2) in the staged words of block walker wl
-    auto bit = [&](int wl, int p) -> uint32_t {
+    // occupation bit of spin orbital p (< N2) of block walker wl in the staged words sb
+    auto bit = [&](const uint32_t *sb, int wl, int p) -> uint32_t {
         const int s = p >= M, k = p - s * M;
-        return (s_bits[wl * nW2 + s * nw + (k >> 5)] >> (k & 31)) & 1u;
+        return (sb[wl * nW2 + s * nw + (k >> 5)] >> (k & 31)) & 1u;
     };
 
-    for (int blk = 0; blk < nblk; ++blk) {
-        const int buf = blk & 1, w0 = w_begin + blk * kJB;
-        // stage the block's occupation words and weight digits
-        for (int i = tid; i < kJB * nW2; i += kThreads) {
-            const int wl = i / nW2, k = i - wl * nW2;
-            s_bits[i] = w0 + wl < w_end ? bits[(size_t)(w0 + wl) * nW2 + k] : 0u;
+    // the next blocks' occupation words and weights travel in registers: block b + 1 is stored to
+    // shared memory and block b + 2 loaded while block b is built, so global latency overlaps
+    uint32_t rb[2];
+    long long rc;
+    auto load_block = [&](int b) {
+        const int w0 = w_begin + b * kJB;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = tid + u * kThreads, wl = i / nW2, k = i - wl * nW2;
+            rb[u] = (b < nblk && i < kJB * nW2 && w0 + wl < w_end) ? bits[(size_t)(w0 + wl) * nW2 + k] : 0u;
+        }
+        const int wl = tid & (kJB - 1), o = tid / kJB;
+        rc = (b < nblk && tid < kJB * n_sets && w0 + wl < w_end) ? cq[(size_t)o * W + w0 + wl] : 0;
+    };
+    auto store_block = [&](int sb) {
+        uint32_t *sbits = s_bits + sb * kJB * 16;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = tid + u * kThreads;
+            if (i < kJB * nW2) sbits[i] = rb[u];
         }
         if (tid < kJB * n_sets) {
             const int wl = tid & (kJB - 1), o = tid / kJB;
-            long long x = w0 + wl < w_end ? cq[(size_t)o * W + w0 + wl] : 0;
+            float *sdig = s_dig + sb * 2 * kJDig * kJB;
+            long long x = rc;
 #pragma unroll
             for (int l = 0; l < kJDig; ++l) {
                 const int d = (int)(signed char)(x & 0xFF);
-                s_dig[(o * kJDig + l) * kJB + wl] = (float)d;
+                sdig[(o * kJDig + l) * kJB + wl] = (float)d;
                 x = (x - d) >> 8;
             }
         }
+    };
+    load_block(0);
+    store_block(0);
+    load_block(1);
+    __syncthreads();
+
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int buf = blk & 1, sb = blk & 1;
         if ((pending >> buf) & 1u) {   // the MMAs that last read this buffer (block blk - 2)
             if (!mbar_wait(&mbar[buf], (phase >> buf) & 1u)) abort_flag = 1;
             phase ^= 1u << buf;
             pending &= ~(1u << buf);
         }
-        __syncthreads();
-        if (abort_flag) break;
+        const uint32_t *cur_bits = s_bits + sb * kJB * 16;
+        const float *cur_dig = s_dig + sb * 2 * kJDig * kJB;
         unsigned char *At = base + (size_t)buf * buf_bytes, *Bt = At + kJA;
         // A[p][w] = n_w[128 P + p]: 16-byte chunk e = 4 walkers of one row (core-matrix order)
         for (int e = tid; e < 128 * kJB / 4; e += kThreads) {
@@ -374,8 +397,8 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
             const int p = P * 128 + rg * 8 + r8;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (p < N2) {
-                v.x = (float)bit(kc * 4 + 0, p); v.y = (float)bit(kc * 4 + 1, p);
-                v.z = (float)bit(kc * 4 + 2, p); v.w = (float)bit(kc * 4 + 3, p);
+                v.x = (float)bit(cur_bits, kc * 4 + 0, p); v.y = (float)bit(cur_bits, kc * 4 + 1, p);
+                v.z = (float)bit(cur_bits, kc * 4 + 2, p); v.w = (float)bit(cur_bits, kc * 4 + 3, p);
             }
             *(float4 *)(At + (uint32_t)e * 16) = v;
         }
@@ -384,23 +407,26 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
             const int q = Q * 32 + lane, kc = warp;
             uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
             if (q < N2) {
-                m0 = 0u - bit(kc * 4 + 0, q); m1 = 0u - bit(kc * 4 + 1, q);
-                m2 = 0u - bit(kc * 4 + 2, q); m3 = 0u - bit(kc * 4 + 3, q);
+                m0 = 0u - bit(cur_bits, kc * 4 + 0, q); m1 = 0u - bit(cur_bits, kc * 4 + 1, q);
+                m2 = 0u - bit(cur_bits, kc * 4 + 2, q); m3 = 0u - bit(cur_bits, kc * 4 + 3, q);
             }
             for (int o = 0; o < n_sets; ++o) {
                 unsigned char *Bo = Bt + (size_t)o * kJBset;
 #pragma unroll
                 for (int l = 0; l < kJDig; ++l) {
-                    const uint4 d = *(const uint4 *)(s_dig + (o * kJDig + l) * kJB + kc * 4);
+                    const uint4 d = *(const uint4 *)(cur_dig + (o * kJDig + l) * kJB + kc * 4);
                     const int row = l * 32 + lane;
                     *(uint4 *)(Bo + core_off(row, kc * 4, kJB / 4)) = make_uint4(d.x & m0, d.y & m1, d.z & m2, d.w & m3);
                 }
             }
         }
+        store_block(sb ^ 1);     // block blk + 1
+        load_block(blk + 2);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        if (abort_flag) break;
         if (tid == 0) {
             const uint32_t idesc = make_idesc(128, 256);
             const uint32_t lbo = 128, sbo = (kJB / 4) * 128;
@@ -490,7 +516,7 @@ void grad_j_umma_chunks(int W, int M, int nsm, int *chunk, int *n_chunks) {
 
 size_t grad_j_umma_smem(int mode) {
     const size_t buf = kJA + (size_t)(mode ? 2 : 1) * kJBset;
-    return 1024 + 2 * buf + sizeof(uint32_t) * kJB * 16 + sizeof(float) * 2 * kJDig * kJB;
+    return 1024 + 2 * buf + 2 * (sizeof(uint32_t) * kJB * 16 + sizeof(float) * 2 * kJDig * kJB);
 }
 
 vmc_status launch_grad_J_umma(vmc_ctx *ctx, int W, int M, const uint32_t *bits, const long long *cq, int mode,
