@@ -281,10 +281,11 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
 // sum_l D_l 256^l in 64-bit integers with wrapping arithmetic; the chunk's true sum is below
 // 2^62 in magnitude, so the wrapped result is exact.
 //
-// CTA = (tile, walker chunk).  Tile = 128 spin orbitals p (MMA rows) x 32 spin orbitals q, with
-// every (p, q <= ...) block that holds some p <= q.  MMA columns j = 256 o + 32 l + q' (weight
-// set o, digit l, q = 32 Q + q'); one or two N = 256 accumulators in tensor memory.  Walkers are
-// staged 32 at a time (the K dimension) into double-buffered K-major core-matrix tiles.
+// CTA = (tile, walker chunk).  Tile (P, Q) = spin orbitals p in [128 P, 128 P + 128) (MMA rows) x
+// q in [32 Q, 32 Q + 32), for every such block that holds some p <= q (Q >= 4 P).  MMA columns
+// j = 256 o + 32 l + q' (weight set o, digit l, q = 32 Q + q'); one or two N = 256 accumulators in
+// tensor memory.  Walkers are staged 32 at a time (the K dimension) into double-buffered K-major
+// core-matrix tiles.
 constexpr int kJB = 32;                 // walkers per K block
 constexpr int kJDig = 8;                // base-256 digits of a 64-bit weight
 constexpr int kJMaxChunk = 65536;       // walkers per chunk: 128 x 65536 = 2^23 < 2^24
