@@ -40,9 +40,24 @@ def test_binding_exposes_the_same_names():
 
 def test_null_arguments_are_rejected_without_a_gpu(libvmc):
     libvmc.vmc_walkers_sizes.restype = ct.c_int
-    out = (ct.c_int64 * 9)()
+    out = (ct.c_int64 * 10)()                                              # int64_t out[10]
     assert libvmc.vmc_walkers_sizes(4, 0, 1, 1, None, out) == 1          # M < 1
     assert libvmc.vmc_walkers_sizes(4, 10, 5, 5, None, out) == 0
     assert list(out)[:3] == [4 * 2 * 1, 4 * 10, 4 * 10]
     libvmc.vmc_lists_info.restype = ct.c_int
     assert libvmc.vmc_lists_info(None, None, None, None) == 1
+
+
+def test_binding_constants_match_the_header():
+    """Option numbers, precision and status codes in the binding are the header's values."""
+    from paper_1807_10633_gb300 import vmc
+    text = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "vmc.h").read_text(), flags=re.S)
+    defines = dict((k, int(v)) for k, v in re.findall(r"#define\s+(VMC_OPT_[A-Z0-9_]+)\s+(\d+)", text))
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(VMC_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert defines and enums
+    for k, v in defines.items():
+        assert getattr(vmc, k) == v, k
+    assert (vmc.VMC_FP64, vmc.VMC_MIXED) == (enums["VMC_FP64"], enums["VMC_MIXED"])
+    for k, v in enums.items():
+        if k.startswith("VMC_ERR_") or k == "VMC_OK":
+            assert vmc._STATUS[v] == k[len("VMC_"):], k
