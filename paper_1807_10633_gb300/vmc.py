@@ -96,12 +96,43 @@ def _ptr(t) -> int | None:
     if t is None:
         return None
     if isinstance(t, torch.Tensor):
-        assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
         return t.data_ptr()
     if isinstance(t, np.ndarray):
-        assert t.flags.c_contiguous
+        if not t.flags.c_contiguous:
+            raise ValueError("arrays passed to the library must be C-contiguous")
         return t.ctypes.data
     return int(t)
+
+
+_F64 = (torch.float64,)
+_CODES = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+
+
+def _need(t, name: str, n: int, dtypes=_F64):
+    """Check a device-tensor argument before its pointer crosses the ABI, where a wrong dtype, size
+    or device would let a kernel read or write past the buffer.  None (an absent optional output)
+    and raw integer pointers pass unchecked: the caller vouches for those."""
+    if t is None or isinstance(t, int):
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a CUDA tensor, got {type(t).__name__}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {' or '.join(map(str, dtypes))}")
+    if t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {n} needed")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+
+
+def _need_grad(walkers, dJ, dCa, dCb, prefix=""):
+    N2 = 2 * walkers.M
+    _need(dJ, prefix + "dJ", N2 * N2)
+    _need(dCa, prefix + "dC_alpha", walkers.M * walkers.n_alpha)
+    _need(dCb, prefix + "dC_beta", walkers.M * walkers.n_beta)
 
 
 def _check(ctx, st: int):
@@ -170,44 +201,67 @@ def vmc_walkers_refresh(ctx, lists, params, walkers):
 
 
 def vmc_log_psi(ctx, walkers, params, out):
+    _need(out, "out", walkers.W)
     _check(ctx, lib().vmc_log_psi(ctx, ct.byref(walkers), ct.byref(params), _ptr(out)))
 
 
 def vmc_local_energy(ctx, lists, params, walkers, eps_run, e_loc, t_res):
+    _need(e_loc, "e_loc", walkers.W)
+    _need(t_res, "t_res", walkers.W)
     _check(ctx, lib().vmc_local_energy(ctx, lists, ct.byref(params), ct.byref(walkers), float(eps_run),
                                        _ptr(e_loc), _ptr(t_res)))
 
 
 def vmc_ctmc_step(ctx, lists, params, walkers, seed, move_code):
+    _need(move_code, "move_code", walkers.W, _CODES)
     _check(ctx, lib().vmc_ctmc_step(ctx, lists, ct.byref(params), ct.byref(walkers), int(seed),
                                     _ptr(move_code)))
 
 
 def vmc_grad_logpsi(ctx, walkers, w, dJ, dCa, dCb):
+    _need(w, "w", walkers.W)
+    _need_grad(walkers, dJ, dCa, dCb)
     _check(ctx, lib().vmc_grad_logpsi(ctx, ct.byref(walkers), _ptr(w), _ptr(dJ), _ptr(dCa), _ptr(dCb)))
 
 
 def vmc_amsgrad_update(ctx, p, g, m, n, alpha, beta1, beta2):
+    _need(p, "p", 0)
+    for t, name in ((g, "g"), (m, "m"), (n, "n")):
+        _need(t, name, p.numel())
     _check(ctx, lib().vmc_amsgrad_update(ctx, _ptr(p), _ptr(g), _ptr(m), _ptr(n), p.numel(),
                                          float(alpha), float(beta1), float(beta2)))
 
 
 def vmc_walker_reduce(ctx, W, t_res, e_loc, out):
+    _need(t_res, "t_res", W)
+    _need(e_loc, "e_loc", W)
+    _need(out, "out", 2)
     _check(ctx, lib().vmc_walker_reduce(ctx, W, _ptr(t_res), _ptr(e_loc), _ptr(out)))
 
 
 def vmc_accumulate_gradient(ctx, walkers, t_res, e_loc, AO, AEO, sums):
     """AO, AEO: (dJ, dCa, dCb) tensors each."""
+    _need(t_res, "t_res", walkers.W)
+    _need(e_loc, "e_loc", walkers.W)
+    _need_grad(walkers, *AO, prefix="AO.")
+    _need_grad(walkers, *AEO, prefix="AEO.")
+    _need(sums, "sums", 2)
     _check(ctx, lib().vmc_accumulate_gradient(ctx, ct.byref(walkers), _ptr(t_res), _ptr(e_loc),
                                               *(_ptr(x) for x in AO), *(_ptr(x) for x in AEO), _ptr(sums)))
 
 
 def vmc_energy_gradient(ctx, sums, A_O, A_EO, g):
+    _need(sums, "sums", 2)
+    _need(g, "g", 0)
+    _need(A_O, "A_O", g.numel())
+    _need(A_EO, "A_EO", g.numel())
     _check(ctx, lib().vmc_energy_gradient(ctx, g.numel(), _ptr(sums), _ptr(A_O), _ptr(A_EO), _ptr(g)))
 
 
 def vmc_grad_logpsi_noalloc(walkers, w, dJ, dCa, dCb, stream=None):
     """Context-free, allocation-free variant of vmc_grad_logpsi (see include/vmc.h)."""
+    _need(w, "w", walkers.W)
+    _need_grad(walkers, dJ, dCa, dCb)
     s = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else (stream or 0)
     st = lib().vmc_grad_logpsi_noalloc(ct.byref(walkers), _ptr(w), _ptr(dJ), _ptr(dCa), _ptr(dCb), s)
     if st != 0:
@@ -274,8 +328,8 @@ class Walkers:
 
 
 def params_struct(J: torch.Tensor, Ca: torch.Tensor, Cb: torch.Tensor) -> vmc_params:
-    for t in (J, Ca, Cb):
-        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    for t, name in ((J, "J"), (Ca, "C_alpha"), (Cb, "C_beta")):
+        _need(t, name, 0)
     return vmc_params(_ptr(J), _ptr(Ca), _ptr(Cb))
 
 
@@ -421,7 +475,8 @@ class LogPsi(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, J, Ca, Cb, engine: Engine):
-        prm = params_struct(J.contiguous(), Ca.contiguous(), Cb.contiguous())
+        Jc, Cac, Cbc = J.contiguous(), Ca.contiguous(), Cb.contiguous()   # alive until the call is queued
+        prm = params_struct(Jc, Cac, Cbc)
         out = torch.zeros(engine.W, dtype=torch.float64, device=J.device)
         vmc_log_psi(engine.ctx, engine.walkers.struct(), prm, out)
         ctx.engine = engine
