@@ -44,6 +44,26 @@ MUTANTS = [
     ("residence time not inverted",
      "*t_res = 1.0 / ((double)qh + (double)ql * 0x1p-64);", "*t_res = (double)qh + (double)ql * 0x1p-64;",
      P.test_ctmc_choice_distribution),
+    ("row-exchange sign dropped from the LU determinant",
+     "            sgn = -sgn;\n", "\n", P.test_direct_ratios_equal_table_ratios),
+    ("sorting parity dropped from the in-place ratio",
+     "return (inv & 1) ? -minor : minor;", "return minor;", _brute_h4),
+    ("transposed inverse in G = C C_occ^-1",
+     "acc += C[(size_t)k * ns + x] * t->Ainv[sg][(size_t)x * ns + cc];",
+     "acc += C[(size_t)k * ns + x] * t->Ainv[sg][(size_t)cc * ns + x];", _brute_h4),
+    ("forward substitution skips the last column of L",
+     "for (int c = 0; c < r; ++c) b[r] -= work[(size_t)r * n + c] * b[c];",
+     "for (int c = 0; c < r - 1; ++c) b[r] -= work[(size_t)r * n + c] * b[c];", _brute_h4),
+    ("E_core dropped from the diagonal energy",
+     "double ed = s->e_core;", "double ed = 0.0;", _brute_h4),
+    ("one-body Jastrow term dropped from the gradient",
+     "dJ[(size_t)p * N2 + p] += weight;", "dJ[(size_t)p * N2 + p] += 0.0;",
+     P.test_energy_gradient_matches_exact_derivative),
+    ("Philox Weyl constant off by one",
+     "W1 = 0xBB67AE8584CAA73BULL", "W1 = 0xBB67AE8584CAA73AULL",
+     lambda: P.test_philox_matches_numpy((1807, 123456), (99, 1, 2, 3))),
+    ("fixed-point rate with 52 instead of 53 bits",
+     "(uint64_t)ldexp(f, 53);", "(uint64_t)ldexp(f, 52);", P.test_ctmc_choice_distribution),
     ("AMSGrad without the running maximum",
      "v[k] = v[k] > cand ? v[k] : cand;", "v[k] = cand;", P.test_amsgrad_hand_recurrence),
     ("AMSGrad with the usual (not the paper's) beta1 convention",
