@@ -38,7 +38,9 @@ def build(force: bool = False) -> Path:
 class _System(ct.Structure):
     _fields_ = [("M", ct.c_int), ("n_alpha", ct.c_int), ("n_beta", ct.c_int),
                 ("h1", ct.c_void_p), ("eri", ct.c_void_p), ("e_core", ct.c_double),
-                ("J", ct.c_void_p), ("Ca", ct.c_void_p), ("Cb", ct.c_void_p)]
+                ("J", ct.c_void_p), ("Ca", ct.c_void_p), ("Cb", ct.c_void_p),
+                ("n_corr", ct.c_int), ("corr_off", ct.c_void_p), ("corr_sites", ct.c_void_p),
+                ("val_off", ct.c_void_p), ("corr_val", ct.c_void_p)]
 
 
 MOVE_DTYPE = np.dtype([("kind", np.int32), ("i", np.int32), ("j", np.int32), ("a", np.int32),
@@ -63,6 +65,8 @@ def lib():
         L.orc_ctmc_choose.restype = ct.c_int
         L.orc_grad_logpsi.argtypes = [P, P, D, P, P, P]
         L.orc_grad_logpsi.restype = ct.c_int
+        L.orc_grad_cps.argtypes = [P, P, D, P]
+        L.orc_grad_cps.restype = None
         L.orc_amsgrad.argtypes = [P, P, P, P, L64, D, D, D]
         L.orc_amsgrad.restype = None
         L.orc_philox4x64.argtypes = [P, P, P]
@@ -89,9 +93,10 @@ def occ_lists_to_n(occ: np.ndarray, M: int, n_alpha: int) -> np.ndarray:
 
 
 class Oracle:
-    """FP64 oracle bound to one Hamiltonian and one set of wavefunction parameters."""
+    """FP64 oracle bound to one Hamiltonian and one set of wavefunction parameters; ``cps`` (a
+    ``systems.CPS``) adds the correlator product of Sec. III.A to the pair Jastrow."""
 
-    def __init__(self, system, params):
+    def __init__(self, system, params, cps=None):
         self.M = system.M
         self.n_alpha, self.n_beta = system.n_alpha, system.n_beta
         self._keep = dict(
@@ -101,8 +106,20 @@ class Oracle:
             Ca=np.ascontiguousarray(params.C_alpha, dtype=np.float64),
             Cb=np.ascontiguousarray(params.C_beta, dtype=np.float64))
         k = self._keep
+        n_corr = 0
+        cp = [None] * 4
+        if cps is not None and len(cps.sites):
+            n_corr = len(cps.sites)
+            k["corr_off"] = np.concatenate([[0], np.cumsum([len(x) for x in cps.sites])]).astype(np.int32)
+            k["corr_sites"] = np.ascontiguousarray(np.concatenate(cps.sites), dtype=np.int32)
+            k["val_off"] = np.concatenate([[0], np.cumsum([len(v) for v in cps.values])]).astype(np.int64)
+            k["corr_val"] = np.ascontiguousarray(np.concatenate(cps.values), dtype=np.float64)
+            for x, v in zip(cps.sites, cps.values):
+                assert len(v) == 4 ** len(x) and np.all((0 <= np.asarray(x)) & (np.asarray(x) < self.M))
+            cp = [_p(k["corr_off"]), _p(k["corr_sites"]), _p(k["val_off"]), _p(k["corr_val"])]
+        self.n_corr_values = int(k["corr_val"].size) if n_corr else 0
         self._s = _System(self.M, self.n_alpha, self.n_beta, _p(k["h1"]), _p(k["eri"]),
-                          float(system.e_core), _p(k["J"]), _p(k["Ca"]), _p(k["Cb"]))
+                          float(system.e_core), _p(k["J"]), _p(k["Ca"]), _p(k["Cb"]), n_corr, *cp)
         self.move_cap = 1 << 16
 
     @property
@@ -147,6 +164,12 @@ class Oracle:
         rc = lib().orc_grad_logpsi(self.sref, _p(n), weight, _p(dJ), _p(dCa), _p(dCb))
         if rc:
             raise ArithmeticError("singular determinant")
+
+    def grad_cps(self, n: np.ndarray, weight: float, dc: np.ndarray):
+        """dc (all correlator coefficients, concatenated) += weight * d ln psi(n) / d c."""
+        n = np.ascontiguousarray(n, dtype=np.uint8)
+        assert dc.dtype == np.float64 and dc.flags.c_contiguous and dc.size == self.n_corr_values
+        lib().orc_grad_cps(self.sref, _p(n), weight, _p(dc))
 
     def sweep(self, n: np.ndarray, eps: float, seed: int, steps: np.ndarray, n_threads: int = 0):
         """One CTMC step for every walker; n (W, 2M) and steps (W,) are updated in place."""

@@ -57,6 +57,14 @@ typedef struct {
     const double *J;    /* (2M)*(2M), read for p <= q */
     const double *Ca;   /* M*n_alpha */
     const double *Cb;   /* M*n_beta */
+    /* Correlator product (Sec. III.A), optional (n_corr = 0: none).  Correlator l covers the
+       spatial sites corr_sites[corr_off[l] .. corr_off[l+1]) and holds 4^k coefficients at
+       corr_val[val_off[l] ..], indexed by sum_t (n_alpha(site_t) + 2 n_beta(site_t)) 4^t. */
+    int n_corr;
+    const int *corr_off;      /* n_corr + 1 */
+    const int *corr_sites;
+    const long *val_off;      /* n_corr + 1 */
+    const double *corr_val;
 } orc_system;
 
 typedef struct {
@@ -185,6 +193,24 @@ static double jastrow_log(const orc_system *s, const uint8_t *n) {
     return acc;
 }
 
+/* Fock-state index of correlator l in determinant n: site t contributes n_alpha + 2 n_beta
+   times 4^t */
+static long corr_index(const orc_system *s, const uint8_t *n, int l) {
+    long idx = 0, w = 1;
+    for (int e = s->corr_off[l]; e < s->corr_off[l + 1]; ++e, w *= 4) {
+        const int site = s->corr_sites[e];
+        idx += w * (n[site] + 2 * n[s->M + site]);
+    }
+    return idx;
+}
+
+/* C[n] = product over the correlators of c_l[n_l]  (1 without correlators) */
+static double cps_value(const orc_system *s, const uint8_t *n) {
+    double v = 1.0;
+    for (int l = 0; l < s->n_corr; ++l) v *= s->corr_val[s->val_off[l] + corr_index(s, n, l)];
+    return v;
+}
+
 /* occupied spatial orbitals of spin sigma in ascending order */
 static int occ_of_spin(const orc_system *s, const uint8_t *n, int sigma, int *occ) {
     int c = 0;
@@ -208,7 +234,8 @@ static double slater_det(const orc_system *s, const uint8_t *n, int sigma, doubl
     return d;
 }
 
-/* psi(n) = exp(lnC[n]) det C^alpha[n] det C^beta[n]  (Sec. III.A with the pair Jastrow) */
+/* psi(n) = exp(lnJ[n]) C[n] det C^alpha[n] det C^beta[n]  (Sec. III.A: the pair Jastrow and, when
+   present, the correlator product) */
 double orc_psi(const orc_system *s, const uint8_t *n) {
     const int nmax = (s->n_alpha > s->n_beta ? s->n_alpha : s->n_beta) + 1;
     double *w1 = (double *)malloc(sizeof(double) * nmax * nmax);
@@ -217,6 +244,7 @@ double orc_psi(const orc_system *s, const uint8_t *n) {
     double da = slater_det(s, n, 0, w1, w2, piv);
     double db = slater_det(s, n, 1, w1, w2, piv);
     double r = exp(jastrow_log(s, n)) * da * db;
+    if (s->n_corr) r *= cps_value(s, n);
     free(w1); free(w2); free(piv);
     return r;
 }
@@ -340,6 +368,7 @@ long orc_local_energy(const orc_system *s, const uint8_t *n_in, double eps, int 
     memset(&t, 0, sizeof(t));
     if (tables_build(s, n, &t)) { tables_free(&t); free(n); free(m); return -1; }
     const double lnC_n = jastrow_log(s, n);
+    const double cps_n = cps_value(s, n);
     const double psi_n = direct ? orc_psi(s, n) : 0.0;
 
     /* diagonal: E_core + sum_i h_ii + 1/2 sum_{i != j} <ij||ij> */
@@ -376,6 +405,7 @@ long orc_local_energy(const orc_system *s, const uint8_t *n_in, double eps, int 
                 int sg = spin_of(s, i);
                 int from = spat(s, i), to = spat(s, a);
                 ratio = spin_ratio(&t, sg, 1, &from, &to, M) * exp(jastrow_log(s, m) - lnC_n);
+                if (s->n_corr) ratio *= cps_value(s, m) / cps_n;
             }
             acc += hel * ratio;
             if (moves) {
@@ -426,6 +456,7 @@ long orc_local_energy(const orc_system *s, const uint8_t *n_in, double eps, int 
                             ratio = spin_ratio(&t, 0, 1, &fa, &ta, M) *
                                     spin_ratio(&t, 1, 1, &fb, &tb, M) * jr;
                         }
+                        if (s->n_corr) ratio *= cps_value(s, m) / cps_n;
                     }
                     acc += hel * ratio;
                     if (moves) {
@@ -546,6 +577,18 @@ int orc_grad_logpsi(const orc_system *s, const uint8_t *n, double weight,
     }
     tables_free(&t);
     return 0;
+}
+
+/*
+ * Adds weight * d ln psi(n) / d c_l[k] = weight * delta(k, n_l) / c_l[k] to dc (laid out like
+ * corr_val): psi is linear in each coefficient, and only the coefficient of the Fock state the
+ * determinant puts on the correlator's sites enters psi(n) (Sec. III.A-B).
+ */
+void orc_grad_cps(const orc_system *s, const uint8_t *n, double weight, double *dc) {
+    for (int l = 0; l < s->n_corr; ++l) {
+        const long k = s->val_off[l] + corr_index(s, n, l);
+        dc[k] += weight / s->corr_val[k];
+    }
 }
 
 /* ---------------------------------------------------------------- AMSGrad, Eqs. (m1), (m2) */

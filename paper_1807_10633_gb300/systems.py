@@ -314,6 +314,51 @@ def make_params(sys: System, seed: int = MASTER_SEED, j_scale: float = 0.01,
 # ---------------------------------------------------------------------------------------
 # Starting determinants (the paper is silent)
 # ---------------------------------------------------------------------------------------
+# ---------------------------------------------------------------------------------------
+# Correlator product (Sec. III.A): local correlators of at most five sites, one centred on every
+# site (Sec. IV.B-C).  The pair Jastrow above is the special case of one- and two-site correlators.
+# ---------------------------------------------------------------------------------------
+@dataclass
+class CPS:
+    """Correlator l covers the spatial sites ``sites[l]`` and holds ``4 ** len(sites[l])``
+    coefficients ``values[l]``, indexed by sum_t (n_alpha(site_t) + 2 n_beta(site_t)) 4**t."""
+    sites: list
+    values: list
+
+
+def correlator_sites(sys: System, size: int = 5) -> list:
+    """Sites of the local correlator centred on each site: on a chain the `size` consecutive
+    sites around it (clipped at the ends), on a ring the same with periodic wrap, on a 2-D
+    lattice the site and its four neighbours."""
+    M = sys.M
+    Lx, Ly = sys.meta.get("Lx"), sys.meta.get("Ly")
+    h = size // 2
+    out = []
+    for c in range(M):
+        if Lx is not None and Ly is not None and Ly > 1:
+            x, y = c % Lx, c // Lx
+            cand = [c, y * Lx + (x + 1) % Lx, y * Lx + (x - 1) % Lx, ((y + 1) % Ly) * Lx + x,
+                    ((y - 1) % Ly) * Lx + x]
+        elif Lx is not None:
+            cand = [(c + d) % M for d in range(-h, h + 1)]
+        else:
+            cand = list(range(max(0, c - h), min(M, c + h + 1)))
+        sites = []
+        for q in cand:
+            if q not in sites:
+                sites.append(q)
+        out.append(np.array(sites, dtype=np.int32))
+    return out
+
+
+def make_cps(sys: System, size: int = 5, seed: int = MASTER_SEED, noise: float = 0.05) -> CPS:
+    """Seeded correlator coefficients 1 + noise * N(0, 1) on the local correlators."""
+    rng = np.random.default_rng(seed)
+    sites = correlator_sites(sys, size)
+    values = [1.0 + noise * rng.normal(size=4 ** len(st)) for st in sites]
+    return CPS(sites, values)
+
+
 def _dpp_rows(C: np.ndarray, B: int, rng: np.random.Generator) -> np.ndarray:
     """B independent draws of n rows of C (M x n) with probability proportional to
     det(C[rows])^2: sequential sampling of the projection determinantal point process onto the

@@ -94,6 +94,18 @@ def psi_all(n: np.ndarray, M: int, prm) -> np.ndarray:
     return np.exp(lnC) * da * db
 
 
+def cps_factor(n: np.ndarray, M: int, cps) -> np.ndarray:
+    """prod over correlators of c_l[state of its sites], each site's state n_alpha + 2 n_beta read
+    as a base-4 digit (first site least significant)."""
+    out = np.ones(len(n))
+    for sites, vals in zip(cps.sites, cps.values):
+        idx = np.zeros(len(n), dtype=np.int64)
+        for t, site in enumerate(sites):
+            idx += (4 ** t) * (n[:, site].astype(np.int64) + 2 * n[:, M + site].astype(np.int64))
+        out *= np.asarray(vals)[idx]
+    return out
+
+
 def singles_bound(sys) -> np.ndarray:
     """S_ia over spatial orbitals (spin independent): |h_ia| + sum over all spin orbitals j."""
     e = sys.eri

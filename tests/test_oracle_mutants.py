@@ -8,6 +8,8 @@ from pathlib import Path
 import pytest
 
 import oracle
+from paper_1807_10633_gb300 import systems as S
+from tests import test_oracle_cps as C
 from tests import test_oracle_pins as P
 
 SRC = Path(oracle.__file__).with_name("vmc_oracle.c")
@@ -15,6 +17,10 @@ SRC = Path(oracle.__file__).with_name("vmc_oracle.c")
 
 def _brute_h4():
     P.test_eloc_eps0_matches_brute_hchain(P._h4)
+
+
+def _cps_brute_h4():
+    C.test_cps_eloc_eps0_matches_brute_all_dets(lambda: S.hchain(4))
 
 
 # (mistake, exact source line fragment, replacement, the pin that must fail)
@@ -64,6 +70,17 @@ MUTANTS = [
      lambda: P.test_philox_matches_numpy((1807, 123456), (99, 1, 2, 3))),
     ("fixed-point rate with 52 instead of 53 bits",
      "(uint64_t)ldexp(f, 53);", "(uint64_t)ldexp(f, 52);", P.test_ctmc_choice_distribution),
+    ("alpha and beta swapped in a correlator's site state",
+     "idx += w * (n[site] + 2 * n[s->M + site]);", "idx += w * (2 * n[site] + n[s->M + site]);",
+     C.test_pair_jastrow_written_as_correlators_gives_the_same_energies),
+    ("correlator digits in base 2 instead of 4",
+     "++e, w *= 4)", "++e, w *= 2)", _cps_brute_h4),
+    ("correlator ratio left out of the doubles",
+     "spin_ratio(&t, 1, 1, &fb, &tb, M) * jr;\n                        }\n"
+     "                        if (s->n_corr) ratio *= cps_value(s, m) / cps_n;",
+     "spin_ratio(&t, 1, 1, &fb, &tb, M) * jr;\n                        }", _cps_brute_h4),
+    ("d ln psi / d c without the 1/c",
+     "dc[k] += weight / s->corr_val[k];", "dc[k] += weight;", C.test_cps_gradient_matches_finite_differences),
     ("AMSGrad without the running maximum",
      "v[k] = v[k] > cand ? v[k] : cand;", "v[k] = cand;", P.test_amsgrad_hand_recurrence),
     ("AMSGrad with the usual (not the paper's) beta1 convention",
