@@ -146,3 +146,33 @@ def test_correlator_sites_follow_the_lattice():
     lat = S.correlator_sites(S.hubbard(4, 4))
     assert sorted(lat[5]) == [1, 4, 5, 6, 9] and all(len(x) == 5 for x in lat)
     assert sorted(lat[0]) == [0, 1, 3, 4, 12]             # periodic neighbours
+
+
+def test_cps_move_ratios_are_brute_force_psi_ratios():
+    """Every screened move's psi(m)/psi(n) -- the CTMC rate up to its sign (Sec. II.B) -- equals
+    the ratio of the brute-force amplitudes with correlators, so the rates and the residence time
+    of a CPS-Slater walker follow from the same ratios as its local energy."""
+    sys_ = S.hchain(6)
+    prm, cps = _case(sys_, seed=31, j_scale=0.05)
+    dets, _ = brute.hamiltonian(sys_)
+    n_all = brute.occupations(dets, sys_.M)
+    psi = brute.psi_all(n_all, sys_.M, prm) * brute.cps_factor(n_all, sys_.M, cps)
+    weights = np.arange(2 * sys_.M, dtype=np.uint64)
+    orc = Oracle(sys_, prm, cps)
+    rng = np.random.default_rng(5)
+    checked = 0
+    for d in rng.choice(len(n_all), 10, replace=False):
+        n = n_all[d]
+        _, _, mv = orc.local_energy(n, 1e-4)
+        for o in mv:
+            m = n.copy()
+            m[o["i"]] = 0
+            m[o["a"]] = 1
+            if o["kind"] == 2:
+                m[o["j"]] = 0
+                m[o["b"]] = 1
+            idx = np.searchsorted(dets, (m.astype(np.uint64) << weights).sum())
+            ref = psi[idx] / psi[d]
+            assert abs(o["ratio"] - ref) <= 1e-11 * max(1.0, abs(ref))
+            checked += 1
+    assert checked > 500
