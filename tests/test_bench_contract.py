@@ -46,3 +46,12 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     (line,) = _lines(r.stdout)
     assert line["impl"] == "reference" and line["n_gpus"] == 2
+
+
+def test_ncu_counters_describe_the_committed_local_energy_kernel():
+    """The DRAM/L2/instruction counters bench.py reports for the local-energy kernel were taken on
+    the kernel source with this digest; the committed source still has it (else bench.py would
+    report traffic as null and the counters would need a new capture)."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert bench.eloc_source_digest() == bench.ELOC_COUNTERS["sha256"]
