@@ -274,12 +274,13 @@ vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const d
 
 /*
  * vmc_grad_logpsi without any allocation and without a context (the paper has no counterpart;
- * it serves callers that may not allocate device memory: code running during CUDA-graph stream
- * capture, or deployments whose device memory is owned by another allocator or fixed up front).
+ * it serves callers that may not allocate device memory: services whose device memory belongs to
+ * another allocator's pool, deployments whose footprint is fixed up front, and host loops that
+ * must not stall on the synchronisation cudaMalloc/cudaFree may cause).
  * Computes the same sums as vmc_grad_logpsi (accumulated into d_dJ, d_dC_alpha, d_dC_beta) for
  * weights d_w [W], using a library-owned 16 MiB device scratch array instead of a workspace.
- * Limit: 256 + 8 W (rounded up to 256 B) + max(64 M^2, 16 M n_max) bytes must fit in 16 MiB,
- * and n_max <= 128; otherwise VMC_ERR_ARG.  The first call on a device looks up the scratch
+ * Limit: 256 + 8 W (rounded up to 256 B) + max(32 M^2, 16 M n_max) bytes must fit in 16 MiB,
+ * and 1 <= n_max <= 128 (n_max = max(n_alpha, n_beta)); otherwise VMC_ERR_ARG.  The first call on a device looks up the scratch
  * array's address (cudaGetSymbolAddress) with that device current: make it before any stream
  * capture.  All calls share the array: calls that overlap on the GPU race.  Work is queued on
  * `cuda_stream` (a cudaStream_t, NULL = legacy default stream).

@@ -1,8 +1,9 @@
 // vmc_grad_logpsi_noalloc: the vector-Jacobian product of ln psi without any allocation.
 //
-// Some callers cannot allocate device memory at all: code that runs while a stream is being
-// captured into a CUDA graph, services that give a framework's pooling allocator sole control
-// of the device, or fixed-footprint deployments that reserve every byte up front.  This entry
+// Some callers cannot allocate device memory at all: services that give a framework's pooling
+// allocator sole control of the device (a cudaMalloc behind its back can fail or fragment its
+// pool), fixed-footprint deployments that reserve every byte up front, and host loops that must
+// not stall (cudaMalloc and cudaFree may synchronise with the device).  This entry
 // point needs neither cudaMalloc nor a context: its scratch space (fixed-point weights and
 // per-chunk partial sums) is a file-scope device array of VMC_NOALLOC_SCRATCH_BYTES that every
 // GPU loading the library holds until the process exits.  The caller still passes the walker
@@ -180,7 +181,7 @@ extern "C" vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *Wk, const doubl
     if (Wk->precision != VMC_FP64 && Wk->precision != VMC_MIXED) return VMC_ERR_ARG;
     const int W = Wk->W, M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta, N2 = 2 * M;
     const int nmax = na > nb ? na : nb;
-    if (nmax > 128) return VMC_ERR_ARG;
+    if (nmax < 1 || nmax > 128) return VMC_ERR_ARG;
     // scratch layout: [exponent | pad to 256] [cq: W int64] [partials]
     const size_t head = 256 + (((size_t)W * 8 + 255) & ~(size_t)255);
     const size_t jchunk_bytes = (size_t)N2 * N2 * 8, cchunk_bytes = (size_t)2 * M * nmax * 8;

@@ -61,3 +61,14 @@ def test_binding_constants_match_the_header():
     for k, v in enums.items():
         if k.startswith("VMC_ERR_") or k == "VMC_OK":
             assert vmc._STATUS[v] == k[len("VMC_"):], k
+
+
+def test_noalloc_gradient_rejects_zero_electrons_without_a_gpu(libvmc):
+    """With no electron of either spin there is no orbital block to size the scratch by: the call
+    must return VMC_ERR_ARG from its host checks (no CUDA call happens before them)."""
+    from paper_1807_10633_gb300 import vmc
+    fake = 256                                     # never dereferenced: the host check comes first
+    ws = vmc.vmc_walkers(8, 4, 0, 0, vmc.VMC_FP64, *([fake] * 10))
+    libvmc.vmc_grad_logpsi_noalloc.restype = ct.c_int
+    assert libvmc.vmc_grad_logpsi_noalloc(ct.byref(ws), ct.c_void_p(fake), ct.c_void_p(fake),
+                                          ct.c_void_p(fake), ct.c_void_p(fake), None) == 1
