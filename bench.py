@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--eps-sweep", default="", help="comma-separated eps values: run the eps / size study "
                     "(cost per 1000 samples of H chains) instead of the benchmark")
     ap.add_argument("--study-systems", default="H20,H40,H80,H160")
+    ap.add_argument("--repeats", type=int, default=3,
+                    help="timed loops of K steps (each followed by an end-to-end loop); the median is reported")
     return ap.parse_args()
 
 
@@ -128,14 +130,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ncu counters of one k_local_energy launch (mixed form, H160, eps 1e-6), per walker: DRAM bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum), L2 bytes (lts__t_sectors.sum x 32) and warp
-# instructions (smsp__inst_executed.sum), from the
-# capture summarised in profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel
-# source with this digest only; any later change of the kernel reports traffic as null.
-ELOC_COUNTERS = {"sha256": "0071176d3d14e0a9233f27dcff5dc8dfe80122665c11af35ec7c7af87b905f33",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80665.8, "l2_bytes_per_walker": 803356.0,
-                 "warp_inst_per_walker": 311870.6}
+# ncu counters of one k_local_energy launch (mixed form, H160, eps 1e-6, 4,096 walkers), per walker:
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum), L2 bytes (lts__t_sectors.sum x 32) and
+# warp instructions (smsp__inst_executed.sum), from the capture summarised in
+# profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel source with this digest
+# only; any later change of the kernel's file reports traffic as null until it is captured again.
+ELOC_COUNTERS = {"sha256": "08ef7d7e55c8c317a66163701104adf6d95e5d5008addcdee0b735877975771d",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80504.0, "l2_bytes_per_walker": 801764.7,
+                 "warp_inst_per_walker": 311871.0}
 
 
 def eloc_source_digest() -> str:
@@ -146,25 +148,28 @@ def eloc_source_digest() -> str:
 
 
 def l2_probe_gbs(dev) -> float:
-    """L2 bandwidth probe: copy between two 24 MB buffers that stay in the 129 MB L2 (read + write bytes)."""
+    """L2 read bandwidth: the library's read-only probe kernel over a 48 MB buffer that stays in the
+    129 MB L2 (16-byte loads through L2, bypassing L1), best of five timed launches of 20 passes."""
     import torch
-    n = 24 * 1024 * 1024 // 4
-    a = torch.ones(n, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    best = None
-    for _ in range(5):
-        t0.record()
-        for _ in range(20):
-            b.copy_(a)
-        t1.record()
-        torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1) / 20
-        best = ms if best is None else min(best, ms)
-    return 2 * a.numel() * 4 / (best * 1e-3) / 1e9
+    from paper_1807_10633_gb300 import vmc
+    buf = torch.ones(48 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = vmc.vmc_create(dev.index, stream)
+    try:
+        vmc.vmc_probe_l2_read(ctx, buf, 2)                 # brings the buffer into L2
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(5):
+            t0.record(stream)
+            vmc.vmc_probe_l2_read(ctx, buf, 20)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            best = ms if best is None else min(best, ms)
+    finally:
+        vmc.vmc_destroy(ctx)
+    return 20 * buf.numel() * 4 / (best * 1e-3) / 1e9
 
 
 def measured_peaks():
@@ -176,7 +181,7 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------- our arm
-def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
+def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
     import torch
     from paper_1807_10633_gb300 import vmc
 
@@ -197,6 +202,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     W, N2, M = eng.W, 2 * sys_.M, sys_.M
     n_singles, n_same, n_opp = vmc.vmc_lists_info(eng.lists)
     eloc_threads = vmc.Batch([eng]).autotune()    # threads per walker CTA for the local energy
+    e_start, _ = eng.local_energy()               # every form starts from the same determinants
+    e_start = e_start.cpu().numpy().copy()
     np_ = eng.n_params
     f64 = dict(dtype=torch.float64, device=dev)
     red, AO, AEO, sums = D.sums_buffer(np_, dev)   # the walker sums: one buffer, one exchange
@@ -309,9 +316,14 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     vmc.vmc_sync(eng.ctx)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
-    ms, launches = timed_loop(e2e=False, it0=1000)
+    dev_ms, e2e_ms = [], []
+    for r in range(args.repeats):                # device-timed and end-to-end loops interleaved
+        ms_r, launches = timed_loop(e2e=False, it0=1000 + 2 * r * args.steps)
+        dev_ms.append(ms_r)
+        e2e_ms.append(timed_loop(e2e=True, it0=1000 + (2 * r + 1) * args.steps)[0])
     clk = clocks.stop()
     vmc.vmc_sync(eng.ctx)
+    ms, ms_e2e = statistics.median(dev_ms), statistics.median(e2e_ms)
     # local-energy launch time: CUDA events around each launch of one eager step
     torch.cuda.synchronize()
     for it in range(2):
@@ -319,27 +331,40 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     torch.cuda.synchronize()
     vmc.vmc_sync(eng.ctx)
     eloc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_pairs)
-    ms_e2e, _ = timed_loop(e2e=True, it0=2000)
-    vmc.vmc_sync(eng.ctx)
     energy = float(sums[1].item() / sums[0].item())
 
-    # algorithmic HBM bytes of one local-energy launch (walker state that must be read/written)
+    # Algorithmic bytes of one local-energy launch, the per-eval figure of the scope table:
+    #   B_eval = K_d b_d + K_s b_s + (F reads of the free singles) + B_state
+    # with K_d, K_s the double and single list entries each walker's walk reads, measured by the
+    # library (vmc_screened_moves) on the walkers as the timed run left them; b_d = 8 B mixed /
+    # 12 B FP64 (a, b, v), b_s = 12 / 16 B; one Fock-sum element per free single (this design keeps
+    # them per walker instead of re-reading O(N_e) integral rows); B_state = the walker state the
+    # launch reads and writes.
     esz = 8 if precision == vmc.VMC_FP64 else 4
     na, nb = sys_.n_alpha, sys_.n_beta
-    ne = na + nb
-    ng = (ne + 31) // 32 + sum((ne - 1 - x + 31) // 32 for x in range(ne - 1))
-    occ_now = eng.walkers.occ_list.view(torch.int16).cpu().numpy().astype(np.int64).reshape(W, ne)
-    f_read = 8.0 * float(np.mean(s_cnt[occ_now].sum(axis=1)))   # F entries of occupied singles
-    per_walker = (esz * ((M - na) * na + (M - nb) * nb + N2)   # G virtual rows + Jastrow sums
-                  + 2 * (2 * M) + 4 * 2 * ((M + 31) // 32)        # occupied / virtual lists, bits
-                  + f_read + 8                                    # Fock sums of occupied singles, e_diag
-                  + 16 + 16 * ng)                                 # E_L, t, rate-group sums written
-    bytes_launch = per_walker * W
+    ng = eng_groups(sys_, eng)
+    n_moves, walked = eng.move_counts()
+    k_s, k_d = float(walked[:, 0].mean()), float(walked[:, 1].mean())
+    b_d, b_s = (12, 16) if precision == vmc.VMC_FP64 else (8, 12)
+    state = (esz * ((M - na) * na + (M - nb) * nb + N2)       # G virtual rows + Jastrow sums
+             + 2 * (2 * M) + 8                                 # orbital map, e_diag
+             + 16 + (16 + 8) * ng)                             # E_L, t; rate sums and energy partials
+    free_s = float(np.mean(singles_free(eng, n_moves)))
+    per_eval = k_d * b_d + k_s * b_s + free_s * esz + state
+    bytes_launch = per_eval * W
     achieved = bytes_launch / (eloc_ms * 1e-3) / 1e9
     evals = W * args.sweeps * args.steps
+    spread = lambda xs: (max(xs) - min(xs)) / statistics.median(xs)
     res = dict(value=evals / (ms * 1e-3), ms_per_step=ms / args.steps, ms_e2e=ms_e2e / args.steps,
                e2e_value=evals / (ms_e2e * 1e-3), eloc_ms=eloc_ms, eloc_bytes=bytes_launch,
                eloc_gbs=achieved, launches=launches, clocks=clk, energy=energy,
+               repeats=dict(n=args.repeats, ms_per_step=[x / args.steps for x in dev_ms],
+                            e2e_ms_per_step=[x / args.steps for x in e2e_ms],
+                            spread=spread(dev_ms), e2e_spread=spread(e2e_ms)),
+               per_walker=dict(K_d_walked=k_d, K_s_walked=k_s, moves=float(n_moves.mean()),
+                               singles_free=free_s, b_d=b_d, b_s=b_s, state_bytes=state,
+                               bytes_per_eval=per_eval, groups=ng),
+               e_start=e_start,
                lists=dict(singles=n_singles, same=n_same, opposite=n_opp), n_params=np_, eloc_threads=eloc_threads,
                h2d=np_ * 8, d2h=(np_ + 2) * 8)
     del graph
@@ -348,6 +373,20 @@ def run_form(args, sys_, prm, occ, precision, rank, world, s_cnt, gj32=False):
     torch.cuda.set_stream(torch.cuda.default_stream(dev))
     torch.cuda.empty_cache()
     return res
+
+
+def eng_groups(sys_, eng) -> int:
+    """Warp groups per walker of the local energy (the rate store's groups): singles blocks of 32
+    spin orbitals plus the row groups of the pair band (equal to the library's count)."""
+    from paper_1807_10633_gb300 import vmc
+    return vmc.vmc_lists_layout(eng.lists)["n_groups"]
+
+
+def singles_free(eng, n_moves):
+    """Free singles per walker: moves that are singles, from one walker sample's move codes."""
+    k = min(eng.W, 64)
+    per, _, _ = eng.screened_moves(0, k)
+    return [int(((c & 3) == 1).sum()) for c, _, _ in per]
 
 
 BATCH_SYSTEMS = [("hubbard4x4", 0.0), ("hubbard6x6", 0.0), ("hubbard8x8", 0.0), ("hubbard10x10", 0.0),
@@ -470,17 +509,6 @@ def eps_study(args):
                       "form": "mixed", "rows": len(rows), "exponent_vs_orbitals": fits}), flush=True)
 
 
-def singles_counts(sys_, eps):
-    """Length of every spatial singles list at eps (used for the byte count only)."""
-    e = sys_.eri
-    Jt = np.einsum("iakk->iak", e)
-    Kt = np.einsum("ikka->iak", e)
-    Sia = np.abs(sys_.h1) + np.abs(Jt - Kt).sum(-1) + np.abs(Jt).sum(-1)
-    np.fill_diagonal(Sia, 0.0)
-    cnt = (Sia > eps).sum(axis=1)
-    return cnt
-
-
 def cpu_sample_default() -> int:
     """Walkers in the oracle sample: 8 per host core (at most 16 cores), about 10-20 s at H160."""
     return 8 * max(1, min(os.cpu_count() or 1, 16))
@@ -493,7 +521,7 @@ def cpu_baseline(args, sys_, prm, occ, sample: int):
     n = np.ascontiguousarray(oracle.occ_lists_to_n(occ[:sample], sys_.M, sys_.n_alpha))
     ctr = np.zeros(sample, dtype=np.uint64)
     t = time.perf_counter()
-    orc.sweep(n, args.eps, args.seed, ctr, n_threads=nt)
+    el, _, _, _ = orc.sweep(n, args.eps, args.seed, ctr, n_threads=nt)
     dt = time.perf_counter() - t
     # one thread on a few of the same walkers (the oracle's single-core rate)
     s1 = max(1, min(sample, 4))
@@ -505,7 +533,8 @@ def cpu_baseline(args, sys_, prm, occ, sample: int):
                 sample=f"{sample} walkers x 1 CTMC step (E_L + choice + move) of the same workload, "
                        f"FP64 oracle, OpenMP over walkers, {dt:.1f} s",
                 single_thread={"value": s1 / dt1, "unit": UNIT, "cores": 1,
-                               "sample": f"{s1} walkers x 1 CTMC step on one thread, {dt1:.1f} s"})
+                               "sample": f"{s1} walkers x 1 CTMC step on one thread, {dt1:.1f} s"},
+                e_loc=el)
 
 
 def main():
@@ -535,7 +564,6 @@ def main():
     prm = S.make_params(sys_, seed=args.seed)
     # each rank's own walkers (weak scaling: walkers per GPU fixed); rank 0 keeps the 1-GPU inputs
     occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1 + 1000003 * rank)
-    s_cnt = singles_counts(sys_, args.eps)
 
     if args.impl == "reference":
         sample = args.cpu_sample or cpu_sample_default()
@@ -544,6 +572,7 @@ def main():
             vals.append(cpu_baseline(args, sys_, prm, occ, sample))
         v = statistics.median(x["value"] for x in vals)
         cb = dict(vals[0])
+        cb.pop("e_loc")
         cb["value"] = v
         config = dict(config, launch="FP64 CPU oracle, OpenMP over walkers", l2="not applicable (CPU)")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -561,7 +590,7 @@ def main():
     results = {}
     for f in forms:
         results[f] = run_form(args, sys_, prm, occ, vmc.VMC_FP64 if f == "fp64" else vmc.VMC_MIXED, rank, world,
-                              s_cnt, gj32=(f == "mixed_gj32"))
+                              gj32=(f == "mixed_gj32"))
     head = results.get("mixed") or results[forms[0]]
     peak, peak_kind = measured_peaks()
     counters_ok = ("mixed" in results and eloc_source_digest() == ELOC_COUNTERS["sha256"]
@@ -572,6 +601,8 @@ def main():
     sm_mhz = head["clocks"].get("sm_mhz") or head["clocks"].get("sm_max_mhz") or 2070.0
     issue_peak = 4 * props.multi_processor_count * sm_mhz * 1e6 / 1e12     # Twarp-inst/s
     l2_bytes = ELOC_COUNTERS["l2_bytes_per_walker"] * args.walkers if counters_ok else None
+    launch_s = head["eloc_ms"] * 1e-3
+    pw = head["per_walker"]
     scale = world
     line = {"metric": METRIC, "value": head["value"] * scale, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -579,26 +610,31 @@ def main():
             "dtype": "f32" if "mixed" in results else "f64", "data": "synthetic", "config": config,
             "e2e": {"value": head["e2e_value"] * scale, "unit": UNIT, "h2d_bytes_per_step": head["h2d"],
                     "d2h_bytes_per_step": head["d2h"]},
+            "repeats": head["repeats"],
             "gpu_launches": head["launches"],
             "eloc_threads_per_walker_cta": head["eloc_threads"],
             "roofline": {"kernel": "k_local_energy", "bound": "hbm", "achieved": head["eloc_gbs"],
                          "peak": peak, "unit": "GB/s", "frac": head["eloc_gbs"] / peak,
                          "peak_source": peak_kind, "traffic": traffic,
-                         "bytes_per_launch": head["eloc_bytes"], "launch_ms": head["eloc_ms"]},
+                         "bytes_per_launch": head["eloc_bytes"], "launch_ms": head["eloc_ms"],
+                         "bytes": "B_eval = K_d b_d + K_s b_s + free singles x F element + walker state, "
+                                  "K_d and K_s measured per walker by the library (per_walker)",
+                         "per_walker": pw,
+                         "state_only_frac": pw["state_bytes"] * args.walkers / launch_s / 1e9 / peak},
             "issue_roofline": {"kernel": "k_local_energy", "bound": "issue",
                                "achieved": (ELOC_COUNTERS["warp_inst_per_walker"] * args.walkers /
-                                            (head["eloc_ms"] * 1e-3) / 1e12) if counters_ok else None,
+                                            launch_s / 1e12) if counters_ok else None,
                                "peak": issue_peak, "unit": "Twarp-inst/s",
                                "frac": (ELOC_COUNTERS["warp_inst_per_walker"] * args.walkers /
-                                        (head["eloc_ms"] * 1e-3) / 1e12 / issue_peak) if counters_ok else None,
+                                        launch_s / 1e12 / issue_peak) if counters_ok else None,
                                "peak_source": "4 schedulers x SMs x median SM clock under load, one warp "
                                               "instruction per scheduler per clock"},
             "l2_roofline": {"kernel": "k_local_energy", "bound": "l2",
-                            "achieved": (l2_bytes / (head["eloc_ms"] * 1e-3) / 1e9) if l2_bytes else None,
+                            "achieved": (l2_bytes / launch_s / 1e9) if l2_bytes else None,
                             "peak": l2_peak, "unit": "GB/s",
-                            "frac": (l2_bytes / (head["eloc_ms"] * 1e-3) / 1e9 / l2_peak) if l2_bytes else None,
+                            "frac": (l2_bytes / launch_s / 1e9 / l2_peak) if l2_bytes else None,
                             "bytes": "ncu lts__t_sectors x 32 per launch, scaled by walkers",
-                            "peak_source": "24 MB L2-resident copy probe (read + write)"},
+                            "peak_source": "the library's L2-resident read probe (vmc_probe_l2_read, 48 MB)"},
             "clocks": head["clocks"],
             "energy_per_electron": head["energy"] / sys_.n_elec,
             "lists": head["lists"], "n_params": head["n_params"]}
@@ -606,14 +642,29 @@ def main():
         if f != "mixed" or len(results) == 1:
             line[f"{f}_form"] = {"value": r["value"] * scale, "ms_per_step": r["ms_per_step"],
                                  "eloc_ms": r["eloc_ms"], "eloc_gbs": r["eloc_gbs"],
-                                 "e2e_value": r["e2e_value"] * scale, "energy_per_electron": r["energy"] / sys_.n_elec}
+                                 "e2e_value": r["e2e_value"] * scale, "repeats": r["repeats"],
+                                 "energy_per_electron": r["energy"] / sys_.n_elec}
     if "mixed" in results and "fp64" in results:
         line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
+    # error of the mixed forms against the FP64 form, every walker at the common start (mEh / electron)
+    if "fp64" in results:
+        ref = results["fp64"]["e_start"]
+        line["mixed_error"] = {f: {"max_mEh_per_electron": float(np.max(np.abs(r["e_start"] - ref))) * 1e3 / sys_.n_elec,
+                                   "mean_mEh_per_electron": float(np.mean(np.abs(r["e_start"] - ref))) * 1e3 / sys_.n_elec,
+                                   "walkers": int(ref.size), "against": "FP64 form on the GPU, same determinants"}
+                               for f, r in results.items() if f != "fp64"}
     if not args.no_batch:
         line["batched_uneven"] = run_batch(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = args.cpu_sample or cpu_sample_default()
-        line["cpu_baseline"] = cpu_baseline(args, sys_, prm, occ, sample)
+        cb = cpu_baseline(args, sys_, prm, occ, sample)
+        el_orc = cb.pop("e_loc")
+        cb["parity_sample"] = {f: (float(np.max(np.abs(r["e_start"][:sample] - el_orc) / np.maximum(1.0, np.abs(el_orc))))
+                                   if f == "fp64" else
+                                   float(np.max(np.abs(r["e_start"][:sample] - el_orc))) * 1e3 / sys_.n_elec)
+                               for f, r in results.items()}
+        cb["parity_sample_units"] = "fp64: max relative E_L error; mixed forms: max mEh per electron"
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -73,20 +73,53 @@ vmc_status vmc_sync(vmc_ctx *ctx);
  * at the first entry at or below a threshold.  The library also stores, per singles entry,
  * the Coulomb/exchange columns used to keep each walker's single-excitation elements
  * h_ai + sum_{j occ} <aj||ij> up to date, and the diagonal Coulomb/exchange tables.
- *   h_h1 : [M*M] host, h_eri : [M^4] host (dense), e_core : constant added to every E_L.
+ *   h_h1 : [M*M] host.
+ *   h_eri : host, eri_packed = 0: dense [M^4] as above; eri_packed = 1: the 8-fold packed form,
+ *           (pq|rs) at PQ(PQ+1)/2 + RS for PQ >= RS, with pair index pq = p(p+1)/2 + q for
+ *           p >= q (M(M+1)/2 * (M(M+1)/2 + 1) / 2 doubles; 0.66 GB instead of 5.2 GB at M = 160).
+ *           Both forms give identical lists when they hold the same values.
+ *   e_core : constant added to every E_L.
  *   eps  : build threshold (>= 0); later calls may walk with any eps_run >= eps.
  *   M    : 1 <= M <= 256.
  * The lists are built on the host (once per eps, O(M^4 log M)) and copied to the device.
  * Free with vmc_lists_destroy.
  */
 vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double *h_h1, const double *h_eri,
-                                    double e_core, double eps, vmc_lists **out);
+                                    int eri_packed, double e_core, double eps, vmc_lists **out);
 vmc_status vmc_lists_destroy(vmc_lists *lists);
 
 /* Sizes of a list object: number of singles entries (the length of each walker's per-spin
    Fock-sum vector), same-spin and opposite-spin double entries. */
 vmc_status vmc_lists_info(const vmc_lists *lists, int64_t *n_singles, int64_t *n_same,
                           int64_t *n_opp);
+
+/* Work layout of the local energy for these lists: band = the largest |p - q| of a non-empty
+   pair list (the pair candidates of an orbital row), n_groups = the warp groups per walker
+   (singles blocks of 32 spin orbitals and orbital-row groups, in canonical move order); the CTMC
+   rate store holds one 128-bit rate sum and one FP64 energy partial per group and walker. */
+vmc_status vmc_lists_layout(const vmc_lists *lists, int *band, int *n_groups);
+
+/*
+ * Near ties of the screening threshold (Sec. II.A keeps |x| > eps; an item whose magnitude lies
+ * within rounding of eps could be kept or dropped by a different summation order, so it is
+ * reported rather than resolved).  *n_near = the number of screening quantities x with
+ * | |x| - eps | < 1e-12 max(1, eps), counted over spin orbitals: S_ia of every same-spin single
+ * i -> a (a != i) and |<ab||ij>| of every spin-conserving double i<j -> a<b with a, b not in
+ * {i, j}, whether or not the item is kept.  eps = the build eps: the builder's own count;
+ * eps above the build eps by more than the band: counted from the stored entries; otherwise
+ * VMC_ERR_ARG.  Host-only (no device work).
+ */
+vmc_status vmc_lists_near_ties(const vmc_lists *lists, double eps, int64_t *n_near);
+
+/*
+ * The host pass of vmc_build_screened_lists alone (no context, no device): out[0..2] = the
+ * numbers of singles, same-spin and opposite-spin entries, out[3] = the near-tie count of eps (as
+ * vmc_lists_near_ties), out[4] = a 64-bit FNV-1a digest of every host array the device lists are
+ * made from (offsets, keys, orbitals, values, Fock and diagonal tables).  Same arguments and
+ * errors as vmc_build_screened_lists.
+ */
+vmc_status vmc_screened_lists_summary(int M, const double *h_h1, const double *h_eri, int eri_packed,
+                                      double eps, int64_t out[5]);
 
 /*
  * Walker state (Sec. III.B): one determinant per walker and the tables that make every ratio
@@ -193,6 +226,29 @@ vmc_status vmc_local_energy(vmc_ctx *ctx, const vmc_lists *lists, const vmc_para
  */
 vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *lists, const vmc_params *params,
                          vmc_walkers *walkers, uint64_t seed, uint64_t *d_move_code);
+
+/*
+ * The screened move set of Sec. II.A / II.B for walkers w_begin .. w_begin + n_w - 1: every
+ * determinant m connected to the walker's n by a single or double whose list entry survives
+ * eps_run (>= the build eps) and whose target orbitals are empty -- the terms of E_L and the
+ * moves of the CTMC step -- in the canonical order of vmc_ctmc_step.  For walker t of the range:
+ *   d_code[t*cap + k]    uint64  move code as in vmc_ctmc_step
+ *   d_ratio[t*cap + k]   double  psi(m)/psi(n) in the in-place replacement convention (the CTMC
+ *                                rate is its magnitude; its sign differs from the canonically
+ *                                ordered ratio by the permutation parity)
+ *   d_contrib[t*cap + k] double  H_nm psi(m)/psi(n) (phase independent; sum + e_diag = E_L)
+ *   d_count[t]           int64   number of moves of the walker (only the first cap are written)
+ *   d_walked[2t], [2t+1] int64   singles and doubles list entries the walk reads, free or not
+ *                                (NULL: not written)
+ * The values are those vmc_local_energy and vmc_ctmc_step compute (same precision, same
+ * rounding).  A diagnostic and test call: one warp walks each walker.  Calling it with another
+ * eps_run than the last vmc_local_energy invalidates the stored rates (vmc_ctmc_step then
+ * returns VMC_ERR_ARG until vmc_local_energy runs again).
+ */
+vmc_status vmc_screened_moves(vmc_ctx *ctx, const vmc_lists *lists, const vmc_params *params,
+                              const vmc_walkers *walkers, double eps_run, int w_begin, int n_w,
+                              int64_t cap, uint64_t *d_code, double *d_ratio, double *d_contrib,
+                              int64_t *d_count, int64_t *d_walked);
 
 /*
  * Batched launches over several systems of uneven size (for example Hubbard lattices and
@@ -309,6 +365,15 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
 #define VMC_OPT_MIXED_REFRESH_GJ32 4
 #define VMC_OPT_GRAD_J_TENSOR_CORES 5
 vmc_status vmc_set_option(vmc_ctx *ctx, int option, int value);
+
+/*
+ * Measurement helper (no counterpart in the paper): one launch that reads the 16-byte-aligned
+ * device buffer d_buf (bytes, a multiple of 16 is read) `reps` times with 16-byte loads through
+ * L2, bypassing L1, on the context's stream.  Timed with events around it, for a buffer that fits
+ * in L2 and after one warm-up call, bytes * reps / time is the L2 read bandwidth that bounds the
+ * local energy's list traffic (the lists are shared by all walkers and stay in L2).
+ */
+vmc_status vmc_probe_l2_read(vmc_ctx *ctx, const void *d_buf, size_t bytes, int reps);
 
 /* Number of kernel launches this context has issued (for accounting in benchmarks). */
 uint64_t vmc_launch_count(const vmc_ctx *ctx);

@@ -73,6 +73,8 @@ def lib():
         L.orc_philox4x64.restype = None
         L.orc_sweep.argtypes = [P, L64, P, D, U64, P, P, P, P, L64, ct.c_int]
         L.orc_sweep.restype = L64
+        L.orc_near_ties.argtypes = [P, D]
+        L.orc_near_ties.restype = L64
         _lib = L
     return _lib
 
@@ -154,6 +156,11 @@ class Oracle:
         if err:
             raise ArithmeticError(f"{err} walkers failed")
         return el, ed, nm
+
+    def near_ties(self, eps: float) -> int:
+        """Screening quantities (S_ia of same-spin singles, |<ab||ij>| of spin-conserving doubles, over
+        all spin orbitals) within 1e-12 max(1, eps) of the threshold eps."""
+        return int(lib().orc_near_ties(self.sref, float(eps)))
 
     def psi(self, n: np.ndarray) -> float:
         n = np.ascontiguousarray(n, dtype=np.uint8)

@@ -654,3 +654,33 @@ long orc_local_energy_batch(const orc_system *s, long W, const uint8_t *occ, dou
     }
     return n_err;
 }
+
+/* ---------------------------------------------------------------- near ties of the screen (Sec. II.A) */
+/*
+ * Number of screening quantities within rounding of the threshold: | |x| - eps | < 1e-12 max(1, eps),
+ * where the screen keeps |x| > eps.  The items are those of the screened sums over spin orbitals,
+ * independent of any determinant: S_ia for every same-spin pair i != a, and |<ab||ij>| for every
+ * i < j, a < b with a, b not in {i, j} and the spins of (a, b) those of (i, j).
+ */
+long orc_near_ties(const orc_system *s, double eps) {
+    const int N2 = 2 * s->M;
+    const double band = 1e-12 * (eps > 1.0 ? eps : 1.0);
+    long n = 0;
+    for (int i = 0; i < N2; ++i)
+        for (int a = 0; a < N2; ++a) {
+            if (a == i || spin_of(s, a) != spin_of(s, i)) continue;
+            if (fabs(singles_bound(s, i, a) - eps) < band) ++n;
+        }
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : n)
+    for (int i = 0; i < N2; ++i)
+        for (int j = i + 1; j < N2; ++j)
+            for (int a = 0; a < N2; ++a) {
+                if (a == i || a == j) continue;
+                for (int b = a + 1; b < N2; ++b) {
+                    if (b == i || b == j) continue;
+                    if (spin_of(s, a) + spin_of(s, b) != spin_of(s, i) + spin_of(s, j)) continue;
+                    if (fabs(fabs(phys_anti(s, a, b, i, j)) - eps) < band) ++n;
+                }
+            }
+    return n;
+}

@@ -224,6 +224,23 @@ vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, 
     return st;
 }
 
+vmc_status vmc_screened_moves(vmc_ctx *ctx, const vmc_lists *Lc, const vmc_params *P, const vmc_walkers *Wk,
+                              double eps_run, int w_begin, int n_w, int64_t cap, uint64_t *code, double *ratio,
+                              double *contrib, int64_t *count, int64_t *walked) {
+    if (!ctx) return VMC_ERR_ARG;
+    vmc_lists *L = const_cast<vmc_lists *>(Lc);
+    if (!L || !P || !count) return set_err(ctx, VMC_ERR_ARG, "null argument");
+    vmc_status st = check_walkers(ctx, Wk, L);
+    if (st) return st;
+    if (!(eps_run >= L->eps_build)) return set_err(ctx, VMC_ERR_ARG, "eps_run must be >= the build eps");
+    if (w_begin < 0 || n_w < 1 || w_begin > Wk->W - n_w) return set_err(ctx, VMC_ERR_ARG, "walker range outside [0, W)");
+    if (cap < 0 || (cap > 0 && (!code || !ratio || !contrib))) return set_err(ctx, VMC_ERR_ARG, "bad move buffers");
+    if (L->eps_run != eps_run) ctx->rates_valid = 0;   // the stored rates belong to other list lengths
+    st = lists_set_eps(ctx, L, eps_run);
+    if (st) return st;
+    return launch_screened_moves(ctx, L, Wk, w_begin, n_w, cap, code, ratio, contrib, count, walked);
+}
+
 vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items) {
     if (!ctx) return VMC_ERR_ARG;
     for (int k = 0; items && k < n; ++k) {

@@ -86,9 +86,9 @@ struct vmc_lists {
     int M = 0;
     double eps_build = 0.0;
     double eps_run = -1.0;   // eps the effective lengths were computed for
+    int64_t near_ties_build = 0;   // near ties of the build eps over every candidate (Sec. II.A)
     int64_t ns = 0, nds = 0, ndo = 0;
     // host copies of the sorted magnitudes (for effective lengths at a given eps_run)
-    std::string dummy;
     double *h_s_key = nullptr, *h_ds_key = nullptr, *h_do_key = nullptr;
     uint32_t *h_s_off = nullptr, *h_ds_off = nullptr, *h_do_off = nullptr;
     void *dev = nullptr;     // one device allocation holding every array
@@ -208,6 +208,9 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
 vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P,
                             vmc_walkers *Wk, uint64_t seed, const u128 *rates, int n_groups,
                             uint64_t *move_code);
+vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, int w_begin, int n_w,
+                                 int64_t cap, uint64_t *code, double *ratio, double *contrib, int64_t *count,
+                                 int64_t *walked);
 vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items);
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);

@@ -664,6 +664,74 @@ k_ctmc_select_batched(const SysDesc *__restrict__ sys, int n_sys, int total, uin
     select_walker<real>(d.L, d.A, t - d.w_begin, d.rates, seed, d.move_code, status);
 }
 
+// Screened move set of one walker, written out in canonical order (Sec. II.A, II.B): one warp per
+// walker walks the same groups, units and list entries as the local energy (groups in index order,
+// units in lane order, entries in list order) and writes every entry whose targets are free with
+// the ratio and contribution the local energy and the CTMC choice use.  Diagnostic path: it also
+// counts the list entries the walk reads (singles, doubles), free or not.
+template <typename real>
+__global__ void __launch_bounds__(256)
+k_screened_moves(ListsView L, WalkerArgs A, int w_begin, int n_w, int64_t cap, uint64_t *__restrict__ code_out,
+                 double *__restrict__ ratio_out, double *__restrict__ contrib_out, int64_t *__restrict__ count_out,
+                 int64_t *__restrict__ walked_out, unsigned *status) {
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= n_w) return;
+    const int w = w_begin + t;
+    const int lane = threadIdx.x & 31;
+    const Geo geo = make_geo(A.M, A.na, A.nb);
+    const int M = geo.M, N2 = 2 * M;
+    const real *Gw = (const real *)A.G + (size_t)w * geo.g_stride;
+    View<real> V;
+    V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
+    V.E = nullptr; V.S = (const real *)A.S + (size_t)w * N2; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad;
+    V.geo = geo;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int64_t cnt = 0, walked_s = 0, walked_d = 0;
+    unsigned flag = 0;
+    for (int g = 0; g < L.n_groups; ++g) {
+        Unit<real> u;
+        const bool act = setup_unit<real>(L, V, g, lane, u);
+        unsigned mask = __ballot_sync(0xffffffffu, act);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const Unit<real> v = shfl_unit(u, src);
+            if (v.base + v.len > list_size(L, v.kind)) {   // cannot happen: guard, never read
+                flag |= VMC_DEV_INCONSISTENT;
+                continue;
+            }
+            if (v.kind == 0) walked_s += v.len; else walked_d += v.len;
+            for (uint32_t k0 = 0; k0 < v.len; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                real ratio = 0, contrib = 0;
+                int a = -1, b = -1;
+                const bool fr = k < v.len && eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b);
+                const unsigned bal = __ballot_sync(0xffffffffu, fr);
+                if (fr) {
+                    const int64_t p = cnt + __popc(bal & lt_mask);
+                    if (p < cap) {
+                        const uint64_t kind = v.kind == 0 ? 1 : 2;
+                        const uint64_t j10 = kind == 2 ? (uint64_t)v.j : 1023ull, b10 = kind == 2 ? (uint64_t)b : 1023ull;
+                        const size_t o = (size_t)t * (size_t)cap + (size_t)p;
+                        code_out[o] = kind | ((uint64_t)v.i << 2) | (j10 << 12) | ((uint64_t)a << 22) | (b10 << 32);
+                        ratio_out[o] = (double)ratio;
+                        contrib_out[o] = (double)contrib;
+                    }
+                }
+                cnt += __popc(bal);
+            }
+        }
+    }
+    if (lane == 0) {
+        count_out[t] = cnt;
+        if (walked_out) {
+            walked_out[2 * (size_t)t] = walked_s;
+            walked_out[2 * (size_t)t + 1] = walked_d;
+        }
+        if (flag) atomicOr(status, flag);
+    }
+}
+
 // Move update: one CTA per walker (Sec. III.B): diagonal energy, Jastrow sums, Fock sums, then the
 // rank-1 (singles, opposite-spin doubles) or rank-2 Woodbury (same-spin doubles) update of G and
 // AinvT, and the occupation lists, bits and orbital map.
@@ -1123,4 +1191,19 @@ vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *ite
     if (e == cudaSuccess) e = cudaGetLastError();
     ctx->rates_batch.clear();
     return cuda_check(ctx, e, "k_ctmc_*_batched");
+}
+
+vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, int w_begin, int n_w,
+                                 int64_t cap, uint64_t *code, double *ratio, double *contrib, int64_t *count,
+                                 int64_t *walked) {
+    WalkerArgs A = make_args(const_cast<vmc_walkers *>(Wk));
+    const int blocks = (n_w + VMC_WARPS - 1) / VMC_WARPS;
+    if (Wk->precision == VMC_FP64)
+        k_screened_moves<double><<<blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, w_begin, n_w, cap, code, ratio,
+                                                                         contrib, count, walked, ctx->d_status);
+    else
+        k_screened_moves<float><<<blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, w_begin, n_w, cap, code, ratio,
+                                                                        contrib, count, walked, ctx->d_status);
+    ctx->launches += 1;
+    return cuda_check(ctx, cudaGetLastError(), "k_screened_moves");
 }

@@ -159,6 +159,32 @@ def _sgauss_ao_integrals(centers: np.ndarray, charges: np.ndarray, exps: np.ndar
     return S, h, eri
 
 
+def pack_eri(eri: np.ndarray) -> np.ndarray:
+    """Dense (pq|rs) [M^4] -> the 8-fold packed vector: pair index pq = p(p+1)/2 + q (p >= q),
+    element PQ(PQ+1)/2 + RS (PQ >= RS); each element is taken from (pq|rs) with p >= q, r >= s,
+    PQ >= RS.  A storage format only (M(M+1)/2 (M(M+1)/2 + 1)/2 doubles)."""
+    M = eri.shape[0]
+    p, q = np.tril_indices(M)                      # pair PQ = p(p+1)/2 + q in this order
+    P, R = np.tril_indices(p.size)
+    return np.ascontiguousarray(eri[p[P], q[P], p[R], q[R]])
+
+
+def unpack_eri(packed: np.ndarray, M: int) -> np.ndarray:
+    """The 8-fold packed vector of pack_eri -> a dense, exactly 8-fold symmetric [M^4] array."""
+    p, q = np.tril_indices(M)
+    npair = p.size
+    pair = np.zeros((M, M), dtype=np.int64)
+    pair[p, q] = np.arange(npair)
+    pair[q, p] = np.arange(npair)
+    RS = pair.reshape(-1)
+    out = np.empty((M, M, M, M))
+    for a in range(M):                             # one bra orbital at a time: O(M^3) indices
+        PQ = pair[a][:, None]
+        A, B = np.maximum(PQ, RS[None, :]), np.minimum(PQ, RS[None, :])
+        out[a] = packed[A * (A + 1) // 2 + B].reshape(M, M, M)
+    return out
+
+
 def _transform_eri(eri: np.ndarray, X: np.ndarray) -> np.ndarray:
     """(pq|rs) <- sum X[mu,p] X[nu,q] X[la,r] X[si,s] (mu nu|la si).
 
@@ -234,6 +260,9 @@ def hchain(n_atoms: int, spacing: float = 1.8) -> System:
     h1 = 0.5 * (h1 + h1.T)
     eri = _transform_eri(eri_ao, X)
     del eri_ao
+    # the transform leaves (pq|rs) and its symmetric images a few ulps apart; keep one value per
+    # symmetry class so the integrals are exactly 8-fold symmetric (dense and packed input agree)
+    eri = unpack_eri(pack_eri(eri), n_atoms)
     e_core = 0.0
     for A in range(n_atoms):
         for B in range(A + 1, n_atoms):
@@ -362,49 +391,58 @@ def make_cps(sys: System, size: int = 5, seed: int = MASTER_SEED, noise: float =
 def _dpp_rows(C: np.ndarray, B: int, rng: np.random.Generator) -> np.ndarray:
     """B independent draws of n rows of C (M x n) with probability proportional to
     det(C[rows])^2: sequential sampling of the projection determinantal point process onto the
-    column space of C (Hough, Krishnapur, Peres & Virag, 2006).  Returns (B, n) sorted rows."""
+    column space of C (Hough, Krishnapur, Peres & Virag, 2006).  Returns (B, n) sorted rows.
+
+    With Q an orthonormal basis of the column space, row m is drawn at step k with probability
+    proportional to its squared distance from the span of the rows already drawn; the basis u_t of
+    that span is grown by Gram-Schmidt (twice, for orthogonality) and the distances are updated by
+    the projections Q u_k (batched over the B draws with torch's CPU matmul)."""
+    import torch
+
     M, n = C.shape
     Q, _ = np.linalg.qr(C)                          # orthonormal basis of the column space
-    Qb = np.broadcast_to(Q, (B, M, n)).copy()
-    r = np.sum(Qb * Qb, axis=2)                      # squared row norms
+    Qt = torch.from_numpy(np.ascontiguousarray(Q))
+    r = torch.from_numpy(np.broadcast_to(np.sum(Q * Q, axis=1), (B, M)).copy())   # squared distances
+    U = torch.zeros((B, n, n), dtype=torch.float64)
     rows = np.empty((B, n), dtype=np.int64)
-    ar = np.arange(B)
+    ar = torch.arange(B)
     for k in range(n):
-        p = np.clip(r, 0.0, None)
-        p /= p.sum(axis=1, keepdims=True)
-        u = rng.random(B)[:, None]
-        i = np.minimum((np.cumsum(p, axis=1) < u).sum(axis=1), M - 1)
-        rows[:, k] = i
-        v = Qb[ar, i, :]
-        v /= np.linalg.norm(v, axis=1, keepdims=True)
-        proj = np.einsum("bmn,bn->bm", Qb, v)
-        Qb -= proj[:, :, None] * v[:, None, :]
+        p = torch.clamp(r, min=0.0)
+        p /= p.sum(dim=1, keepdim=True)
+        u = torch.from_numpy(rng.random(B))[:, None]
+        i = torch.clamp((torch.cumsum(p, dim=1) < u).sum(dim=1), max=M - 1)
+        rows[:, k] = i.numpy()
+        v = Qt[i].clone()
+        if k:
+            Uk = U[:, :k]
+            for _ in range(2):
+                v -= torch.bmm(Uk.transpose(1, 2), torch.bmm(Uk, v[:, :, None]))[:, :, 0]
+        v /= torch.linalg.norm(v, dim=1, keepdim=True)
+        U[:, k] = v
+        proj = v @ Qt.T
         r -= proj * proj
         r[ar, i] = 0.0
     return np.sort(rows, axis=1)
 
 
 def init_occupations(sys: System, prm: Params, W: int, seed: int = MASTER_SEED + 1,
-                     pool: int = 4096, chunk: int = 512) -> np.ndarray:
+                     chunk: int = 512) -> np.ndarray:
     """Per-walker occupied orbital lists, shape (W, n_alpha + n_beta), uint16, each spin block
     sorted ascending (alpha orbitals, then beta; spatial indices 0..M-1).
 
     Each spin's orbitals are an exact draw from |det C^s[rows]|^2, the distribution the Slater
     part alone would be sampled from, so walkers start at typical, well-conditioned
-    determinants.  At most `pool` distinct starts are drawn; larger W reuse them cyclically."""
+    determinants.  Every walker gets its own draw."""
     rng = np.random.default_rng(seed)
-    P = min(W, pool)
     na, nb = sys.n_alpha, sys.n_beta
-    occ = np.empty((P, na + nb), dtype=np.uint16)
-    for c0 in range(0, P, chunk):
-        c1 = min(P, c0 + chunk)
+    occ = np.empty((W, na + nb), dtype=np.uint16)
+    for c0 in range(0, W, chunk):
+        c1 = min(W, c0 + chunk)
         if na:
             occ[c0:c1, :na] = _dpp_rows(prm.C_alpha, c1 - c0, rng)
         if nb:
             occ[c0:c1, na:] = _dpp_rows(prm.C_beta, c1 - c0, rng)
-    if P == W:
-        return occ
-    return occ[np.arange(W) % P].copy()
+    return occ
 
 
 def occ_to_bits(occ: np.ndarray, M: int, n_alpha: int) -> np.ndarray:

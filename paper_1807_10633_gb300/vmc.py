@@ -63,7 +63,12 @@ def lib() -> ct.CDLL:
             "vmc_set_stream": ([P, P], I),
             "vmc_last_error": ([P], ct.c_char_p),
             "vmc_sync": ([P], I),
-            "vmc_build_screened_lists": ([P, I, P, P, D, D, ct.POINTER(P)], I),
+            "vmc_build_screened_lists": ([P, I, P, P, I, D, D, ct.POINTER(P)], I),
+            "vmc_screened_lists_summary": ([I, P, P, I, D, ct.POINTER(I64)], I),
+            "vmc_lists_near_ties": ([P, D, ct.POINTER(I64)], I),
+            "vmc_lists_layout": ([P, ct.POINTER(I), ct.POINTER(I)], I),
+            "vmc_screened_moves": ([P, P, ct.POINTER(vmc_params), ct.POINTER(vmc_walkers), D, I, I, I64,
+                                    P, P, P, P, P], I),
             "vmc_lists_destroy": ([P], I),
             "vmc_lists_info": ([P, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I64)], I),
             "vmc_walkers_sizes": ([I, I, I, I, P, ct.POINTER(I64)], I),
@@ -78,6 +83,7 @@ def lib() -> ct.CDLL:
             "vmc_energy_gradient": ([P, ct.c_size_t, P, P, P, P], I),
             "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
+            "vmc_probe_l2_read": ([P, P, ct.c_size_t, I], I),
             "vmc_set_option": ([P, I, I], I),
             "vmc_grad_logpsi_noalloc": ([ct.POINTER(vmc_walkers), P, P, P, P, P], I),
             "vmc_local_energy_batch": ([P, I, ct.POINTER(vmc_batch_item)], I),
@@ -166,14 +172,70 @@ def vmc_sync(ctx):
     _check(ctx, lib().vmc_sync(ctx))
 
 
-def vmc_build_screened_lists(ctx, M: int, h1: np.ndarray, eri: np.ndarray, e_core: float, eps: float):
+def eri_form(M: int, eri: np.ndarray) -> int:
+    """0 for dense (pq|rs) [M^4] storage, 1 for the 8-fold packed form (see include/vmc.h)."""
+    npair = M * (M + 1) // 2
+    if eri.size == M ** 4:
+        return 0
+    if eri.size == npair * (npair + 1) // 2:
+        return 1
+    raise ValueError(f"eri: {eri.size} elements is neither M^4 nor the 8-fold packed size for M = {M}")
+
+
+def _integrals(M, h1, eri):
     h1 = np.ascontiguousarray(h1, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
-    assert h1.size == M * M and eri.size == M ** 4
+    if h1.size != M * M:
+        raise ValueError(f"h1: {h1.size} elements, expected {M * M}")
+    return h1, eri, eri_form(M, eri)
+
+
+def vmc_build_screened_lists(ctx, M: int, h1: np.ndarray, eri: np.ndarray, e_core: float, eps: float):
+    """eri dense [M^4] or 8-fold packed (detected from its size)."""
+    h1, eri, packed = _integrals(M, h1, eri)
     out = ct.c_void_p()
-    _check(ctx, lib().vmc_build_screened_lists(ctx, M, _ptr(h1), _ptr(eri), float(e_core), float(eps),
+    _check(ctx, lib().vmc_build_screened_lists(ctx, M, _ptr(h1), _ptr(eri), packed, float(e_core), float(eps),
                                                ct.byref(out)))
     return out
+
+
+def vmc_screened_lists_summary(M: int, h1: np.ndarray, eri: np.ndarray, eps: float) -> dict:
+    """Host pass of the list builder (no device): sizes, near ties and a digest of the lists."""
+    h1, eri, packed = _integrals(M, h1, eri)
+    out = (ct.c_int64 * 5)()
+    st = lib().vmc_screened_lists_summary(M, _ptr(h1), _ptr(eri), packed, float(eps), out)
+    if st != 0:
+        raise VmcError(st, "vmc_screened_lists_summary")
+    return dict(singles=out[0], same=out[1], opposite=out[2], near_ties=out[3], digest=out[4] & (2 ** 64 - 1))
+
+
+def vmc_lists_layout(lists) -> dict:
+    band, ng = ct.c_int(), ct.c_int()
+    st = lib().vmc_lists_layout(lists, ct.byref(band), ct.byref(ng))
+    if st != 0:
+        raise VmcError(st, "vmc_lists_layout")
+    return dict(band=band.value, n_groups=ng.value)
+
+
+def vmc_lists_near_ties(lists, eps: float) -> int:
+    n = ct.c_int64()
+    st = lib().vmc_lists_near_ties(lists, float(eps), ct.byref(n))
+    if st != 0:
+        raise VmcError(st, "vmc_lists_near_ties: eps must be the build eps or above it by more than the band")
+    return n.value
+
+
+def vmc_screened_moves(ctx, lists, params, walkers, eps_run, w_begin, n_w, cap, code, ratio, contrib, count,
+                       walked=None):
+    if cap > 0:
+        _need(code, "code", n_w * cap, _CODES)
+        _need(ratio, "ratio", n_w * cap)
+        _need(contrib, "contrib", n_w * cap)
+    _need(count, "count", n_w, (torch.int64,))
+    _need(walked, "walked", 2 * n_w, (torch.int64,))
+    _check(ctx, lib().vmc_screened_moves(ctx, lists, ct.byref(params), ct.byref(walkers), float(eps_run),
+                                         int(w_begin), int(n_w), int(cap), _ptr(code), _ptr(ratio), _ptr(contrib),
+                                         _ptr(count), _ptr(walked)))
 
 
 def vmc_lists_destroy(lists):
@@ -284,6 +346,11 @@ def vmc_autotune_local_energy(ctx, items) -> int:
 
 def vmc_set_option(ctx, option: int, value: int):
     _check(ctx, lib().vmc_set_option(ctx, option, value))
+
+
+def vmc_probe_l2_read(ctx, buf: torch.Tensor, reps: int):
+    _need(buf, "buf", 0, (buf.dtype,))
+    _check(ctx, lib().vmc_probe_l2_read(ctx, _ptr(buf), buf.numel() * buf.element_size(), int(reps)))
 
 
 def vmc_launch_count(ctx) -> int:
@@ -402,6 +469,40 @@ class Engine:
         dCb = torch.zeros_like(self.Cb) if dCb is None else dCb
         vmc_grad_logpsi(self.ctx, self.walkers.struct(), w.contiguous(), dJ, dCa, dCb)
         return dJ, dCa, dCb
+
+    def move_counts(self, eps_run: float | None = None):
+        """Per walker: the number of screened moves and the singles and doubles list entries the walk
+        reads (vmc_screened_moves with no move buffers), as host arrays (W,) and (W, 2)."""
+        eps_run = self.eps if eps_run is None else eps_run
+        count = torch.zeros(self.W, dtype=torch.int64, device=self.device)
+        walked = torch.zeros(2 * self.W, dtype=torch.int64, device=self.device)
+        vmc_screened_moves(self.ctx, self.lists, self.params, self.walkers.struct(), eps_run, 0, self.W, 0,
+                           None, None, None, count, walked)
+        return count.cpu().numpy(), walked.view(self.W, 2).cpu().numpy()
+
+    def screened_moves(self, w_begin: int = 0, n_w: int | None = None, eps_run: float | None = None,
+                       cap: int = 0):
+        """The screened move set of walkers [w_begin, w_begin + n_w) (vmc_screened_moves), as
+        host arrays: per walker (codes, ratios, contributions) plus the walked entry counts."""
+        n_w = self.W - w_begin if n_w is None else n_w
+        eps_run = self.eps if eps_run is None else eps_run
+        dev = self.device
+        count = torch.zeros(n_w, dtype=torch.int64, device=dev)
+        walked = torch.zeros(2 * n_w, dtype=torch.int64, device=dev)
+        if cap <= 0:   # first pass: the counts size the buffers
+            vmc_screened_moves(self.ctx, self.lists, self.params, self.walkers.struct(), eps_run, w_begin, n_w, 0,
+                               None, None, None, count, walked)
+            cap = max(1, int(count.max().item()))
+        code = torch.zeros(n_w * cap, dtype=torch.int64, device=dev)
+        ratio = torch.zeros(n_w * cap, dtype=torch.float64, device=dev)
+        contrib = torch.zeros(n_w * cap, dtype=torch.float64, device=dev)
+        vmc_screened_moves(self.ctx, self.lists, self.params, self.walkers.struct(), eps_run, w_begin, n_w, cap,
+                           code, ratio, contrib, count, walked)
+        cnt = count.cpu().numpy()
+        c, r, e = (x.view(n_w, cap).cpu().numpy() for x in (code, ratio, contrib))
+        out = [(c[t, :min(cap, cnt[t])].astype(np.uint64), r[t, :min(cap, cnt[t])], e[t, :min(cap, cnt[t])])
+               for t in range(n_w)]
+        return out, cnt, walked.view(n_w, 2).cpu().numpy()
 
     def log_psi(self) -> torch.Tensor:
         out = torch.zeros(self.W, dtype=torch.float64, device=self.device)
