@@ -140,6 +140,12 @@ ELOC_COUNTERS = {"sha256": "08ef7d7e55c8c317a66163701104adf6d95e5d5008addcdee0b7
                  "warp_inst_per_walker": 311871.0}
 
 
+def counters_apply(system: str, eps: float) -> bool:
+    """The captured counters describe this workload and the kernel source as it is now."""
+    return (eloc_source_digest() == ELOC_COUNTERS["sha256"] and system == ELOC_COUNTERS["system"]
+            and eps == ELOC_COUNTERS["eps"])
+
+
 def eloc_source_digest() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -593,8 +599,7 @@ def main():
                               gj32=(f == "mixed_gj32"))
     head = results.get("mixed") or results[forms[0]]
     peak, peak_kind = measured_peaks()
-    counters_ok = ("mixed" in results and eloc_source_digest() == ELOC_COUNTERS["sha256"]
-                   and args.system == ELOC_COUNTERS["system"] and args.eps == ELOC_COUNTERS["eps"])
+    counters_ok = "mixed" in results and counters_apply(args.system, args.eps)
     traffic = ELOC_COUNTERS["dram_bytes_per_walker"] * args.walkers if counters_ok else None
     l2_peak = l2_probe_gbs(torch.device("cuda", torch.cuda.current_device()))
     props = torch.cuda.get_device_properties(torch.cuda.current_device())

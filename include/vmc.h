@@ -154,14 +154,44 @@ typedef struct {
     void *F;
     double *e_diag;
     uint64_t *rng_counter;
+    uint16_t *cps_state;      /* [W][n_corr] coefficient index of every correlator (only with a
+                                 correlator product, see vmc_cps_create; NULL otherwise) */
 } vmc_walkers;
 
-/* Wavefunction parameters, device pointers: J [(2M)*(2M)], C_alpha [M*na], C_beta [M*nb]. */
+typedef struct vmc_cps vmc_cps;       /* device copy of a correlator product's structure */
+
+/*
+ * Wavefunction parameters, device pointers: J [(2M)*(2M)], C_alpha [M*na], C_beta [M*nb].
+ * Optional correlator product (Sec. III.A, the general form of the Jastrow factor): cps (NULL:
+ * none) and its coefficients cps_values [n_values] (FP64, the parameters; layout in
+ * vmc_cps_create).  psi(n) is then multiplied by prod_l c_l[n_l].
+ */
 typedef struct {
     const double *J;
     const double *C_alpha;
     const double *C_beta;
+    const vmc_cps *cps;
+    const double *cps_values;
 } vmc_params;
+
+/*
+ * Correlator product of Sec. III.A: psi(n) = prod_l c_l[n_l] x (pair Jastrow) x det C^a det C^b.
+ * Correlator l covers the spatial sites h_sites[h_off[l] .. h_off[l+1]) (1 to 8 distinct sites
+ * below M; at most 16 correlators may cover one site); its coefficients are c_l[k] for
+ * k = sum_t (n_alpha(site_t) + 2 n_beta(site_t)) 4^t, stored at cps_values[off_l + k] with off_l the
+ * sum of 4^(sites of l') over l' < l.  The library copies the structure (h_off [n_corr + 1],
+ * h_sites, host) to the device and builds per-site lists of the correlators covering each site,
+ * so a move's ratio multiplies c_l[new] / c_l[old] over the correlators that touch the changed
+ * orbitals (Sec. III.B) and the gradient ratio is d ln psi / d c_l[k] = 1/c_l[k] for the k present.
+ * The walkers' state is one 16-bit index per correlator (vmc_walkers.cps_state), set by
+ * vmc_walkers_init / vmc_walkers_refresh and kept up to date by vmc_ctmc_step.  The correlator
+ * product is supported by the per-system calls (not by the batched launches).
+ */
+vmc_status vmc_cps_create(vmc_ctx *ctx, int M, int n_corr, const int32_t *h_off, const int32_t *h_sites,
+                          vmc_cps **out);
+vmc_status vmc_cps_destroy(vmc_cps *cps);
+/* Number of correlators and of coefficients (the length of cps_values). */
+vmc_status vmc_cps_info(const vmc_cps *cps, int *n_corr, int64_t *n_values);
 
 /* Element counts of every walker array for W walkers (for allocation by the caller):
    out[0..9] = occ_bits, occ_list, virt_list, pos, G, AinvT, S, F, e_diag, rng_counter. */
@@ -292,6 +322,24 @@ vmc_status vmc_autotune_local_energy(vmc_ctx *ctx, int n_items, const vmc_batch_
  */
 vmc_status vmc_grad_logpsi(vmc_ctx *ctx, const vmc_walkers *walkers, const double *d_w,
                            double *d_dJ, double *d_dC_alpha, double *d_dC_beta);
+
+/*
+ * Correlator-product block of the vector-Jacobian product (Sec. III.B gradient ratios):
+ *   d_dc[off_l + k] += sum_w w_w / c_l[k]   for the index k = n_l of every correlator l in walker w
+ * (params->cps and walkers->cps_state required; d_dc: [n_values] FP64 device).  The sum is exact
+ * in 64-bit fixed point before the final conversion, so it does not depend on summation order.
+ */
+vmc_status vmc_grad_logpsi_cps(vmc_ctx *ctx, const vmc_walkers *walkers, const vmc_params *params,
+                               const double *d_w, double *d_dc);
+
+/*
+ * The two energy-gradient pieces of the correlator coefficients for one CTMC sweep (as
+ * vmc_accumulate_gradient, whose walker sums d_sums it does not touch):
+ *   d_AO_c += sum_w t_w d ln psi_w / dc,   d_AEO_c += sum_w t_w E_L,w d ln psi_w / dc.
+ */
+vmc_status vmc_accumulate_gradient_cps(vmc_ctx *ctx, const vmc_walkers *walkers, const vmc_params *params,
+                                       const double *d_t_res, const double *d_e_loc, double *d_AO_c,
+                                       double *d_AEO_c);
 
 /*
  * Gradient accumulation for one CTMC sweep (Sec. II.B weights, Eq. grad pieces), one pass:

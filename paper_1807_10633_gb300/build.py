@@ -16,7 +16,7 @@ ROOT = PKG.parent
 SRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libvmc.so"
-SOURCES = ["api.cu", "lists.cu", "walkers.cu", "eloc.cu", "grad.cu", "noalloc.cu", "umma.cu", "probe.cu"]
+SOURCES = ["api.cu", "lists.cu", "walkers.cu", "eloc.cu", "grad.cu", "noalloc.cu", "umma.cu", "probe.cu", "cps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O2",
          "-I", str(ROOT / "include"), "-I", str(SRC)]

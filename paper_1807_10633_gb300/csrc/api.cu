@@ -177,8 +177,12 @@ static vmc_status init_common(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, v
     if (!L || !P || !P->J || !P->C_alpha || !P->C_beta) return set_err(ctx, VMC_ERR_ARG, "null lists or parameters");
     vmc_status st = check_walkers(ctx, Wk, L);
     if (st) return st;
+    st = check_cps(ctx, P, Wk);
+    if (st) return st;
     ctx->rates_valid = 0;
-    return launch_init_walkers(ctx, L, P, Wk, full);
+    st = launch_init_walkers(ctx, L, P, Wk, full);
+    if (st) return st;
+    return launch_cps_state(ctx, P, Wk);
 }
 
 vmc_status vmc_walkers_init(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, vmc_walkers *Wk) {
@@ -197,13 +201,15 @@ vmc_status vmc_local_energy(vmc_ctx *ctx, const vmc_lists *Lc, const vmc_params 
     vmc_status st = check_walkers(ctx, Wk, L);
     if (st) return st;
     if (!(eps_run >= L->eps_build)) return set_err(ctx, VMC_ERR_ARG, "eps_run must be >= the build eps");
+    st = check_cps(ctx, P, Wk);
+    if (st) return st;
     st = lists_set_eps(ctx, L, eps_run);
     if (st) return st;
     const int ng = L->view.n_groups;
     void *rates = nullptr;
     st = ensure_rates(ctx, sizeof(u128) * rate_store_units(Wk->W, ng), &rates);
     if (st) return st;
-    st = launch_local_energy(ctx, L, Wk, e_loc, t_res, (u128 *)rates, ng);
+    st = launch_local_energy(ctx, L, Wk, cps_view(P), e_loc, t_res, (u128 *)rates, ng);
     if (st) return st;
     ctx->rates_walkers = Wk->G;
     ctx->rates_groups = ng;
@@ -219,6 +225,8 @@ vmc_status vmc_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, 
     if (st) return st;
     if (!ctx->rates_valid || ctx->rates_walkers != Wk->G)
         return set_err(ctx, VMC_ERR_ARG, "vmc_local_energy must precede vmc_ctmc_step on the same walkers");
+    st = check_cps(ctx, P, Wk);
+    if (st) return st;
     st = launch_ctmc_step(ctx, L, P, Wk, seed, (const u128 *)ctx->rates, ctx->rates_groups, move_code);
     ctx->rates_valid = 0;
     return st;
@@ -235,10 +243,12 @@ vmc_status vmc_screened_moves(vmc_ctx *ctx, const vmc_lists *Lc, const vmc_param
     if (!(eps_run >= L->eps_build)) return set_err(ctx, VMC_ERR_ARG, "eps_run must be >= the build eps");
     if (w_begin < 0 || n_w < 1 || w_begin > Wk->W - n_w) return set_err(ctx, VMC_ERR_ARG, "walker range outside [0, W)");
     if (cap < 0 || (cap > 0 && (!code || !ratio || !contrib))) return set_err(ctx, VMC_ERR_ARG, "bad move buffers");
+    st = check_cps(ctx, P, Wk);
+    if (st) return st;
     if (L->eps_run != eps_run) ctx->rates_valid = 0;   // the stored rates belong to other list lengths
     st = lists_set_eps(ctx, L, eps_run);
     if (st) return st;
-    return launch_screened_moves(ctx, L, Wk, w_begin, n_w, cap, code, ratio, contrib, count, walked);
+    return launch_screened_moves(ctx, L, Wk, cps_view(P), w_begin, n_w, cap, code, ratio, contrib, count, walked);
 }
 
 vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items) {
@@ -246,6 +256,8 @@ vmc_status vmc_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *ite
     for (int k = 0; items && k < n; ++k) {
         vmc_status st = check_walkers(ctx, items[k].walkers, items[k].lists);
         if (st) return st;
+        if (items[k].params && items[k].params->cps)
+            return set_err(ctx, VMC_ERR_ARG, "the batched launches do not take a correlator product");
     }
     ctx->rates_valid = 0;
     return launch_local_energy_batch(ctx, n, items);
@@ -256,6 +268,8 @@ vmc_status vmc_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items,
     for (int k = 0; items && k < n; ++k) {
         vmc_status st = check_walkers(ctx, items[k].walkers, items[k].lists);
         if (st) return st;
+        if (items[k].params && items[k].params->cps)
+            return set_err(ctx, VMC_ERR_ARG, "the batched launches do not take a correlator product");
     }
     return launch_ctmc_step_batch(ctx, n, items, seed);
 }
@@ -346,7 +360,11 @@ vmc_status vmc_log_psi(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_params *P,
     vmc_status st = check_walkers(ctx, Wk, nullptr);
     if (st) return st;
     if (!P || !P->J || !P->C_alpha || !P->C_beta || !out) return set_err(ctx, VMC_ERR_ARG, "null argument");
-    return launch_log_psi(ctx, Wk, P, out);
+    st = check_cps(ctx, P, Wk);
+    if (st) return st;
+    st = launch_log_psi(ctx, Wk, P, out);
+    if (st) return st;
+    return launch_cps_log_psi(ctx, P, Wk, out);
 }
 
 }  // extern "C"

@@ -82,6 +82,26 @@ struct ListsView {
     double e_core;
 };
 
+// Correlator product (Sec. III.A): device view of the structure plus the coefficient table.
+#define VMC_CPS_MAX_SITES 8        // sites per correlator: 4^8 coefficients, a 16-bit index
+#define VMC_CPS_MAX_PER_SITE 16    // correlators covering one site
+struct CpsView {
+    int n_corr;                    // 0: no correlator product
+    const int32_t *corr_off;       // [n_corr + 1]: sites of correlator l are corr_sites[corr_off[l] ..)
+    const int32_t *corr_sites;
+    const int64_t *val_off;        // [n_corr + 1]: coefficients of l at values[val_off[l] ..], 4^k of them
+    const int32_t *site_off;       // [M + 1]: correlators covering site k are site_ent[site_off[k] ..)
+    const uint32_t *site_ent;      // (l << 16) | 4^t, t = the site's digit position in l; l ascending
+    const double *values;          // the coefficients (parameters), FP64, device
+};
+
+struct vmc_cps {
+    int M = 0, n_corr = 0;
+    int64_t n_values = 0;
+    void *dev = nullptr;           // one device allocation: offsets, sites, site table
+    CpsView view{};                // values == nullptr (passed with the parameters)
+};
+
 struct vmc_lists {
     int M = 0;
     double eps_build = 0.0;
@@ -203,14 +223,15 @@ size_t walker_stride_A(int na, int nb);
 vmc_status launch_refresh_jastrow(vmc_ctx *ctx, vmc_lists *L, const double *J);
 vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P,
                                vmc_walkers *Wk, int full);
-vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk,
+struct CpsView;
+vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk, const CpsView &C,
                                double *e_loc, double *t_res, u128 *rates, int n_groups);
 vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P,
                             vmc_walkers *Wk, uint64_t seed, const u128 *rates, int n_groups,
                             uint64_t *move_code);
-vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, int w_begin, int n_w,
-                                 int64_t cap, uint64_t *code, double *ratio, double *contrib, int64_t *count,
-                                 int64_t *walked);
+vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, const CpsView &C,
+                                 int w_begin, int n_w, int64_t cap, uint64_t *code, double *ratio, double *contrib,
+                                 int64_t *count, int64_t *walked);
 vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items);
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);
@@ -230,3 +251,8 @@ vmc_status launch_walker_reduce(vmc_ctx *ctx, int W, const double *t, const doub
                                 double *out);
 vmc_status launch_log_psi(vmc_ctx *ctx, const vmc_walkers *Wk, const vmc_params *P,
                           double *out);
+// correlator product (cps.cu)
+CpsView cps_view(const vmc_params *P);
+vmc_status check_cps(vmc_ctx *ctx, const vmc_params *P, const vmc_walkers *Wk);
+vmc_status launch_cps_state(vmc_ctx *ctx, const vmc_params *P, vmc_walkers *Wk);
+vmc_status launch_cps_log_psi(vmc_ctx *ctx, const vmc_params *P, const vmc_walkers *Wk, double *out);

@@ -92,6 +92,7 @@ struct WalkerArgs {
     void *G, *AinvT, *S, *F;
     double *e_diag;
     uint64_t *rng;
+    uint16_t *cps;       // [W][n_corr] correlator indices (correlator product only)
 };
 
 struct SysDesc {
@@ -145,7 +146,13 @@ struct View {
                            // from S on the fly)
     const real *S;         // walker S in global (used when E == nullptr)
     const real *F;         // walker F [2][ns_pad]
+    CpsView C;             // correlator product (C.n_corr == 0: none)
+    const uint16_t *cidx;  // [n_corr] the walker's correlator indices
+    const real *cinv;      // [n_corr] 1 / c_l[n_l] (shared), or nullptr: from the coefficients
     Geo geo;
+    __device__ real cinv_of(int l) const {
+        return cinv ? cinv[l] : rrcp((real)__ldg(&C.values[__ldg(&C.val_off[l]) + cidx[l]]));
+    }
     __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }              // p virtual
     __device__ real Eiv(int p) const { return E ? E[p] : rrcp(rexp(S[p])); }       // p occupied
     __device__ bool occ(int p) const { return !(pos[p] & 0x8000); }
@@ -163,6 +170,46 @@ __device__ __forceinline__ int row_cand(const ListsView &L, int i, int t) {
     const int nS = min(L.band, M - 1 - p);
     if (t < nS) return i + 1 + t;
     return M + max(0, p - L.band) + (t - nS);
+}
+
+// Correlator-product ratio prod_l c_l[n_l + delta_l] / c_l[n_l] of the move that empties spin
+// orbitals r0 (and r1) and fills a0 (and a1) (Sec. III.B): the per-site lists of the changed sites
+// are merged in correlator order so every touched correlator is visited once, with delta_l the sum
+// of the digit changes (+-1 alpha, +-2 beta) times 4^(site position).  nx = 2 (single) or 4.
+// A state index outside the correlator's table (an inconsistent state) gives NaN, which the rate
+// check reports.
+template <typename real>
+__device__ __forceinline__ real cps_ratio(const View<real> &V, int r0, int a0, int r1, int a1, int nx) {
+    const int M = V.geo.M;
+    int h[4], e[4], d[4];
+    uint32_t c[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int p = x == 0 ? r0 : (x == 1 ? a0 : (x == 2 ? r1 : a1));
+        const int sp = p >= M ? 1 : 0, site = p - sp * M;
+        d[x] = ((x & 1) ? 1 : -1) * (1 + sp);
+        h[x] = x < nx ? __ldg(&V.C.site_off[site]) : 0;
+        e[x] = x < nx ? __ldg(&V.C.site_off[site + 1]) : 0;
+        c[x] = h[x] < e[x] ? __ldg(&V.C.site_ent[h[x]]) : 0xFFFFFFFFu;
+    }
+    real r = real(1);
+    for (int it = 0; it < 4 * VMC_CPS_MAX_PER_SITE; ++it) {
+        const uint32_t l = min(min(c[0], c[1]), min(c[2], c[3])) >> 16;   // next correlator, ascending
+        if (l == 0xFFFFu) break;
+        int delta = 0;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if ((c[x] >> 16) == l) {
+                delta += d[x] * (int)(c[x] & 0xFFFFu);
+                ++h[x];
+                c[x] = h[x] < e[x] ? __ldg(&V.C.site_ent[h[x]]) : 0xFFFFFFFFu;
+            }
+        const int64_t base = __ldg(&V.C.val_off[l]);
+        const int idx = (int)V.cidx[l] + delta;
+        if (idx < 0 || idx >= (int)(__ldg(&V.C.val_off[l + 1]) - base)) return real(NAN);
+        r = rmul(r, rmul((real)__ldg(&V.C.values[base + idx]), V.cinv_of((int)l)));
+    }
+    return r;
 }
 
 // Set up the unit of lane `lane` in group g.  Returns false if the lane has no active unit.
@@ -256,10 +303,10 @@ __device__ __forceinline__ uint32_t list_size(const ListsView &L, int kind) {
 // ratio = psi(m)/psi(n) of a free entry (in-place replacement convention: the fermionic phases
 // of H and of the ratio cancel) and contrib = H_nm * ratio.  Every kernel evaluates rates with
 // this one sequence of explicitly rounded operations, so they agree bit for bit.
-template <typename real>
+template <typename real, bool kC>
 __device__ __forceinline__ void entry_value(const ListsView &L, const View<real> &V, int kind, int cls, int ci,
                                             int cj, real einv, uint32_t idx, real &ratio, real &contrib, int &A,
-                                            int &B) {
+                                            int &B, int I = -1, int Jo = -1) {
     const int M = V.geo.M;
     if (kind == 0) {
         const int s = cls;
@@ -267,7 +314,8 @@ __device__ __forceinline__ void entry_value(const ListsView &L, const View<real>
         const int a = (int)r.key();
         const real g = V.Grow(s, V.pos[s * M + a] & 0x7FFF)[ci];
         const real w = s ? r.f2() : r.f1();
-        const real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), einv);
+        real rt = rmul(rmul(rmul(g, w), V.Ev(s * M + a)), einv);
+        if (kC) rt = rmul(rt, cps_ratio<real>(V, I, s * M + a, I, s * M + a, 2));
         ratio = rt;
         contrib = rmul(V.F[(size_t)s * L.ns_pad + idx], rt);
         A = s * M + a; B = -1;
@@ -282,7 +330,8 @@ __device__ __forceinline__ void entry_value(const ListsView &L, const View<real>
         const real *rb = V.Grow(s, V.pos[s * M + b] & 0x7FFF);
         const real minor = rsub(rmul(ra[ci], rb[cj]), rmul(ra[cj], rb[ci]));
         const real w = s ? r.f3() : r.f2();
-        const real rt = rmul(rmul(rmul(rmul(minor, w), V.Ev(s * M + a)), V.Ev(s * M + b)), einv);
+        real rt = rmul(rmul(rmul(rmul(minor, w), V.Ev(s * M + a)), V.Ev(s * M + b)), einv);
+        if (kC) rt = rmul(rt, cps_ratio<real>(V, I, s * M + a, Jo, s * M + b, 4));
         ratio = rt;
         contrib = rmul(r.f1(), rt);
         A = s * M + a; B = s * M + b;
@@ -293,18 +342,19 @@ __device__ __forceinline__ void entry_value(const ListsView &L, const View<real>
     const int a = ab & 0xFFFF, b = ab >> 16;
     const real ga = V.Grow(0, V.pos[a] & 0x7FFF)[ci];
     const real gb = V.Grow(1, V.pos[M + b] & 0x7FFF)[cj];
-    const real rt = rmul(rmul(rmul(rmul(rmul(ga, gb), r.f2()), V.Ev(a)), V.Ev(M + b)), einv);
+    real rt = rmul(rmul(rmul(rmul(rmul(ga, gb), r.f2()), V.Ev(a)), V.Ev(M + b)), einv);
+    if (kC) rt = rmul(rt, cps_ratio<real>(V, I, a, Jo, M + b, 4));
     ratio = rt;
     contrib = rmul(r.f1(), rt);
     A = a; B = M + b;
 }
 
 // Evaluate list entry `idx` of unit u.  Returns false if the target orbital(s) are occupied.
-template <typename real>
+template <typename real, bool kC>
 __device__ __forceinline__ bool eval_entry(const ListsView &L, const View<real> &V, const Unit<real> &u,
                                            uint32_t idx, real &ratio, real &contrib, int &A, int &B) {
     if (!entry_free<real>(L, V, u.kind, u.cls, idx)) return false;
-    entry_value<real>(L, V, u.kind, u.cls, u.ci, u.cj, u.einv, idx, ratio, contrib, A, B);
+    entry_value<real, kC>(L, V, u.kind, u.cls, u.ci, u.cj, u.einv, idx, ratio, contrib, A, B, u.i, u.j);
     return true;
 }
 
@@ -331,20 +381,22 @@ __device__ __forceinline__ double warp_sum_acc(float v) {
 // Evaluate cnt queued entries q[0..cnt) of one warp, one per lane (lanes >= cnt idle).  Every entry
 // of one queue has the same kind K (compile time).  Entry code = list index << 5 | unit lane; the
 // unit's columns, 1/(E_i E_j) and kind | spin << 2 are held by that lane (cci, ccj, ceinv, cmeta).
-template <int K, typename real, typename acc_t>
+template <int K, typename real, typename acc_t, bool kC>
 __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real> &V, const uint32_t *q, int cnt,
-                                            int lane, int cci, int ccj, real ceinv, int cmeta, acc_t &e_grp,
-                                            u128 &q_grp, unsigned &flag) {
+                                            int lane, int cci, int ccj, real ceinv, int cmeta, int cii, int cjj,
+                                            acc_t &e_grp, u128 &q_grp, unsigned &flag) {
     const uint32_t code = lane < cnt ? q[lane] : 0u;
     const int src = (int)(code & 31u);
     const int ci = __shfl_sync(0xffffffffu, cci, src);
     const int cj = K == 0 ? 0 : __shfl_sync(0xffffffffu, ccj, src);
     const real einv = __shfl_sync(0xffffffffu, ceinv, src);
     const int cls = K == 2 ? 0 : (__shfl_sync(0xffffffffu, cmeta, src) >> 2);
+    const int oi = kC ? __shfl_sync(0xffffffffu, cii, src) : -1;
+    const int oj = (kC && K != 0) ? __shfl_sync(0xffffffffu, cjj, src) : -1;
     if (lane < cnt) {
         real ratio, contrib;
         int a, b;
-        entry_value<real>(L, V, K, cls, ci, cj, einv, code >> 5, ratio, contrib, a, b);
+        entry_value<real, kC>(L, V, K, cls, ci, cj, einv, code >> 5, ratio, contrib, a, b, oi, oj);
         e_grp += (acc_t)contrib;
         q_grp += rate_of<real>(ratio, &flag);
     }
@@ -355,11 +407,11 @@ __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real>
 // entries are evaluated at once.  Lanes past the end test `sent`, a key naming the unit's own
 // (occupied) orbitals, so the test needs no bounds branch.  pos and the queue are addressed as
 // 32-bit shared-memory addresses.
-template <int K, typename real, typename acc_t>
+template <int K, typename real, typename acc_t, bool kC>
 __device__ __forceinline__ void walk_unit(const ListsView &L, const View<real> &V, uint32_t base, uint32_t len,
                                           int cls, int src, uint32_t sent, uint32_t *wq, int &q, int lane,
-                                          unsigned lt_mask, int cci, int ccj, real ceinv, int cmeta, acc_t &e_grp,
-                                          u128 &q_grp, unsigned &flag) {
+                                          unsigned lt_mask, int cci, int ccj, real ceinv, int cmeta, int cii, int cjj,
+                                          acc_t &e_grp, u128 &q_grp, unsigned &flag) {
     const int M = V.geo.M;
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? 0 : cls * M));
     const uint32_t sB = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? M : cls * M));
@@ -380,17 +432,19 @@ __device__ __forceinline__ void walk_unit(const ListsView &L, const View<real> &
         if (q >= 32) {
             __syncwarp();
             q -= 32;
-            drain_queue<K, real, acc_t>(L, V, wq + q, 32, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+            drain_queue<K, real, acc_t, kC>(L, V, wq + q, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                            flag);
             __syncwarp();
         }
     }
 }
 
 // Local energy of walker w by the whole CTA (any number of warps).  smraw: dynamic shared memory.
-template <typename real>
+template <typename real, bool kC>
 __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs &A, const int w,
                                             double *__restrict__ e_loc, double *__restrict__ t_res,
-                                            u128 *__restrict__ rates, unsigned *status, unsigned char *smraw) {
+                                            u128 *__restrict__ rates, unsigned *status, unsigned char *smraw,
+                                            const CpsView &C = CpsView{}) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarp = nt >> 5;
     const int M = geo.M, n_groups = L.n_groups, n_sgl_groups = (2 * M + 31) / 32;
@@ -403,6 +457,9 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     double *eg = (double *)(rates + (size_t)A.W * n_groups) + (size_t)w * n_groups;
     // per warp: two queues of 64 entry codes (idx << 5 | unit lane): kinds 0/1, and kind 2
     uint32_t *wq = (uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + warp * 128;
+    // correlator product: 1 / c_l[n_l] and the indices n_l, after the queues
+    real *sCinv = (real *)((uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + nwarp * 128);
+    uint16_t *sCidx = (uint16_t *)(sCinv + ((C.n_corr + 3) & ~3));
     __shared__ u128 red_q[32];
     __shared__ int next_group;
 
@@ -425,6 +482,12 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
             sE[p] = (ps & 0x8000) ? e : rrcp(e);
             pos[p] = ps;
         }
+        if (kC)
+            for (int l = tid; l < C.n_corr; l += nt) {
+                const uint16_t k = A.cps[(size_t)w * C.n_corr + l];
+                sCidx[l] = k;
+                sCinv[l] = rrcp((real)C.values[C.val_off[l] + k]);
+            }
         if (tid == 0) next_group = nwarp;
     }
     __syncthreads();
@@ -432,6 +495,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     View<real> V;
     V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
     V.E = sE; V.S = nullptr; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
+    V.C = C; V.cidx = sCidx; V.cinv = sCinv;
     typedef typename AccT<real>::type acc_t;
     u128 q_tot = 0;
     unsigned flag = 0;
@@ -446,7 +510,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
         const bool act = setup_unit<real>(L, V, g, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
         const int cmeta = u.kind | (u.cls << 2);
-        const int cci = u.ci, ccj = u.cj;
+        const int cci = u.ci, ccj = u.cj, cii = u.i, cjj = u.j;
         const real ceinv = u.einv;
         acc_t e_grp = 0;
         u128 q_grp = 0;
@@ -469,24 +533,28 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
                 continue;
             }
             if (kind == 2)
-                walk_unit<2, real, acc_t>(L, V, base, len, cls, src, sent, wq + 64, qn1, lane, lt_mask, cci, ccj,
-                                          ceinv, cmeta, e_grp, q_grp, flag);
+                walk_unit<2, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq + 64, qn1, lane, lt_mask, cci, ccj,
+                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
             else if (kind == 1)
-                walk_unit<1, real, acc_t>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj, ceinv,
-                                          cmeta, e_grp, q_grp, flag);
+                walk_unit<1, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj,
+                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
             else
-                walk_unit<0, real, acc_t>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj, ceinv,
-                                          cmeta, e_grp, q_grp, flag);
+                walk_unit<0, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj,
+                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
         }
         __syncwarp();
         // queue 0 holds singles (singles groups) or same-spin doubles (row groups); queue 1 opposite spin
         if (qn0) {
             if (g < n_sgl_groups)
-                drain_queue<0, real, acc_t>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+                drain_queue<0, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                                flag);
             else
-                drain_queue<1, real, acc_t>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+                drain_queue<1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                                flag);
         }
-        if (qn1) drain_queue<2, real, acc_t>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, e_grp, q_grp, flag);
+        if (qn1)
+            drain_queue<2, real, acc_t, kC>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                            flag);
         __syncwarp();
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
@@ -533,7 +601,17 @@ __global__ void __launch_bounds__(kT, EmB<kT>::v)
 k_local_energy(ListsView L, WalkerArgs A, double *__restrict__ e_loc, double *__restrict__ t_res,
                u128 *__restrict__ rates, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    eloc_walker<real>(L, A, blockIdx.x, e_loc, t_res, rates, status, smraw);
+    eloc_walker<real, false>(L, A, blockIdx.x, e_loc, t_res, rates, status, smraw);
+}
+
+// The same with the correlator product (a separate instantiation, so the pair-Jastrow kernel above
+// is not touched by it).
+template <typename real, int kT>
+__global__ void __launch_bounds__(kT, EmB<kT>::v)
+k_local_energy_cps(ListsView L, WalkerArgs A, CpsView C, double *__restrict__ e_loc, double *__restrict__ t_res,
+                   u128 *__restrict__ rates, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    eloc_walker<real, true>(L, A, blockIdx.x, e_loc, t_res, rates, status, smraw, C);
 }
 
 // Batched launch over several systems (uneven sizes).  CTAs stay resident and take walkers from
@@ -552,7 +630,7 @@ k_local_energy_batched(const SysDesc *__restrict__ sys, int n_sys, int total, in
         int k = 0;
         while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
         const SysDesc &d = sys[k];
-        eloc_walker<real>(d.L, d.A, t - d.w_begin, d.e_loc, d.t_res, d.rates, status, smraw);
+        eloc_walker<real, false>(d.L, d.A, t - d.w_begin, d.e_loc, d.t_res, d.rates, status, smraw);
     }
 }
 
@@ -560,10 +638,11 @@ k_local_energy_batched(const SysDesc *__restrict__ sys, int n_sys, int total, in
 // Selection: one warp per walker.  Scans the walker's group sums (u128), draws Philox, finds the
 // group whose prefix crosses T and re-walks only that group with the same entry code as the
 // local-energy kernel.  Writes the move code (0 = no move) and advances the walker's counter.
-template <typename real>
+template <typename real, bool kC>
 __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerArgs &A, const int w,
                                               const u128 *__restrict__ rates, uint64_t seed,
-                                              uint64_t *__restrict__ move_code, unsigned *status) {
+                                              uint64_t *__restrict__ move_code, unsigned *status,
+                                              const CpsView &C = CpsView{}) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int lane = threadIdx.x & 31;
     const int M = geo.M, N2 = 2 * M, n_groups = L.n_groups;
@@ -600,6 +679,7 @@ __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerAr
         View<real> V;
         V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
         V.E = nullptr; V.S = Sw; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
+        V.C = C; V.cidx = kC ? A.cps + (size_t)w * C.n_corr : nullptr; V.cinv = nullptr;
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, gsel, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -616,7 +696,7 @@ __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerAr
                 int a = -1, b = -1;
                 if (k < v.len) {
                     real ratio, contrib;
-                    if (eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
+                    if (eval_entry<real, kC>(L, V, v, v.base + k, ratio, contrib, a, b)) q = rate_of<real>(ratio, &flag);
                 }
                 const u128 incl2 = warp_incl_scan_u128(q, lane) + carry;
                 const unsigned hit = __ballot_sync(0xffffffffu, k < v.len && q != 0 && incl2 > Tl);
@@ -644,13 +724,13 @@ __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerAr
     }
 }
 
-template <typename real>
+template <typename real, bool kC>
 __global__ void __launch_bounds__(512)
-k_ctmc_select(ListsView L, WalkerArgs A, const u128 *__restrict__ rates, uint64_t seed,
+k_ctmc_select(ListsView L, WalkerArgs A, CpsView C, const u128 *__restrict__ rates, uint64_t seed,
               uint64_t *__restrict__ move_code, unsigned *status) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= A.W) return;
-    select_walker<real>(L, A, w, rates, seed, move_code, status);
+    select_walker<real, kC>(L, A, w, rates, seed, move_code, status, C);
 }
 
 template <typename real>
@@ -661,7 +741,7 @@ k_ctmc_select_batched(const SysDesc *__restrict__ sys, int n_sys, int total, uin
     int k = 0;
     while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
     const SysDesc &d = sys[k];
-    select_walker<real>(d.L, d.A, t - d.w_begin, d.rates, seed, d.move_code, status);
+    select_walker<real, false>(d.L, d.A, t - d.w_begin, d.rates, seed, d.move_code, status);
 }
 
 // Screened move set of one walker, written out in canonical order (Sec. II.A, II.B): one warp per
@@ -669,9 +749,9 @@ k_ctmc_select_batched(const SysDesc *__restrict__ sys, int n_sys, int total, uin
 // units in lane order, entries in list order) and writes every entry whose targets are free with
 // the ratio and contribution the local energy and the CTMC choice use.  Diagnostic path: it also
 // counts the list entries the walk reads (singles, doubles), free or not.
-template <typename real>
+template <typename real, bool kC>
 __global__ void __launch_bounds__(256)
-k_screened_moves(ListsView L, WalkerArgs A, int w_begin, int n_w, int64_t cap, uint64_t *__restrict__ code_out,
+k_screened_moves(ListsView L, WalkerArgs A, CpsView C, int w_begin, int n_w, int64_t cap, uint64_t *__restrict__ code_out,
                  double *__restrict__ ratio_out, double *__restrict__ contrib_out, int64_t *__restrict__ count_out,
                  int64_t *__restrict__ walked_out, unsigned *status) {
     const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -685,6 +765,7 @@ k_screened_moves(ListsView L, WalkerArgs A, int w_begin, int n_w, int64_t cap, u
     V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
     V.E = nullptr; V.S = (const real *)A.S + (size_t)w * N2; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad;
     V.geo = geo;
+    V.C = C; V.cidx = kC ? A.cps + (size_t)w * C.n_corr : nullptr; V.cinv = nullptr;
     const unsigned lt_mask = (1u << lane) - 1u;
     int64_t cnt = 0, walked_s = 0, walked_d = 0;
     unsigned flag = 0;
@@ -705,7 +786,7 @@ k_screened_moves(ListsView L, WalkerArgs A, int w_begin, int n_w, int64_t cap, u
                 const uint32_t k = k0 + lane;
                 real ratio = 0, contrib = 0;
                 int a = -1, b = -1;
-                const bool fr = k < v.len && eval_entry<real>(L, V, v, v.base + k, ratio, contrib, a, b);
+                const bool fr = k < v.len && eval_entry<real, kC>(L, V, v, v.base + k, ratio, contrib, a, b);
                 const unsigned bal = __ballot_sync(0xffffffffu, fr);
                 if (fr) {
                     const int64_t p = cnt + __popc(bal & lt_mask);
@@ -735,10 +816,10 @@ k_screened_moves(ListsView L, WalkerArgs A, int w_begin, int n_w, int64_t cap, u
 // Move update: one CTA per walker (Sec. III.B): diagonal energy, Jastrow sums, Fock sums, then the
 // rank-1 (singles, opposite-spin doubles) or rank-2 Woodbury (same-spin doubles) update of G and
 // AinvT, and the occupation lists, bits and orbital map.
-template <typename real>
+template <typename real, bool kC>
 __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArgs &A, const double *__restrict__ J,
                                              const int w, const uint64_t *__restrict__ move_code,
-                                             unsigned char *smraw) {
+                                             unsigned char *smraw, const CpsView &C = CpsView{}) {
     const Geo geo = make_geo(A.M, A.na, A.nb);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nwarp = nt >> 5;
     const uint64_t code = move_code[w];
@@ -759,6 +840,18 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
     __syncthreads();
     const int kind = (int)(code & 3), I = (int)((code >> 2) & 1023), Jo = (int)((code >> 12) & 1023);
     const int Ao = (int)((code >> 22) & 1023), Bo = (int)((code >> 32) & 1023);
+    // ---- correlator indices: every (changed orbital, covering correlator) adds its digit change
+    if (kC && tid == 0) {
+        uint16_t *ci = A.cps + (size_t)w * C.n_corr;
+        const int chg[4] = {I, Ao, Jo, Bo};
+        for (int x = 0; x < (kind == 2 ? 4 : 2); ++x) {
+            const int sp = chg[x] >= M ? 1 : 0, site = chg[x] - sp * M, dg = ((x & 1) ? 1 : -1) * (1 + sp);
+            for (int h = C.site_off[site]; h < C.site_off[site + 1]; ++h) {
+                const uint32_t ent = C.site_ent[h];
+                ci[ent >> 16] = (uint16_t)((int)ci[ent >> 16] + dg * (int)(ent & 0xFFFFu));
+            }
+        }
+    }
 
     // ---- diagonal energy change (old occupation), FP64
     {
@@ -929,11 +1022,11 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
 // 256 threads per walker; six resident CTAs per SM (<= 40 registers): the update is bound by HBM
 // latency between its barrier-separated phases, so more walkers in flight per SM pay (12 % faster
 // than four per SM at H160, with a few spilled registers)
-template <typename real>
+template <typename real, bool kC>
 __global__ void __launch_bounds__(256, 6)
-k_ctmc_apply(ListsView L, WalkerArgs A, const double *__restrict__ J, const uint64_t *__restrict__ move_code) {
+k_ctmc_apply(ListsView L, WalkerArgs A, CpsView C, const double *__restrict__ J, const uint64_t *__restrict__ move_code) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    apply_walker<real>(L, A, J, blockIdx.x, move_code, smraw);
+    apply_walker<real, kC>(L, A, J, blockIdx.x, move_code, smraw, C);
 }
 
 template <typename real>
@@ -944,7 +1037,7 @@ k_ctmc_apply_batched(const SysDesc *__restrict__ sys, int n_sys) {
     int k = 0;
     while (k + 1 < n_sys && sys[k + 1].w_begin <= t) ++k;
     const SysDesc &d = sys[k];
-    apply_walker<real>(d.L, d.A, d.J, t - d.w_begin, d.move_code, smraw);
+    apply_walker<real, false>(d.L, d.A, d.J, t - d.w_begin, d.move_code, smraw);
 }
 
 }  // namespace
@@ -959,24 +1052,32 @@ static WalkerArgs make_args(vmc_walkers *Wk) {
     A.occ_list = Wk->occ_list; A.virt_list = Wk->virt_list; A.pos = Wk->pos;
     A.G = Wk->G; A.AinvT = Wk->AinvT; A.S = Wk->S; A.F = Wk->F; A.e_diag = Wk->e_diag;
     A.rng = Wk->rng_counter;
+    A.cps = Wk->cps_state;
     return A;
 }
 
 template <typename real, int kT>
 static cudaError_t eloc_launch_t(const vmc_ctx *ctx, int W, size_t smem, const ListsView &L, const WalkerArgs &A,
-                                 double *e_loc, double *t_res, u128 *rates) {
-    cudaError_t e = cudaFuncSetAttribute(k_local_energy<real, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                 const CpsView &C, double *e_loc, double *t_res, u128 *rates) {
+    cudaError_t e;
+    if (C.n_corr) {
+        e = cudaFuncSetAttribute(k_local_energy_cps<real, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_local_energy_cps<real, kT><<<W, kT, smem, ctx->stream>>>(L, A, C, e_loc, t_res, rates, ctx->d_status);
+        return e;
+    }
+    e = cudaFuncSetAttribute(k_local_energy<real, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_local_energy<real, kT><<<W, kT, smem, ctx->stream>>>(L, A, e_loc, t_res, rates, ctx->d_status);
     return e;
 }
 template <typename real>
 static cudaError_t eloc_launch(const vmc_ctx *ctx, int W, size_t smem, const ListsView &L, const WalkerArgs &A,
-                               double *e_loc, double *t_res, u128 *rates) {
+                               const CpsView &C, double *e_loc, double *t_res, u128 *rates) {
     switch (ctx->eloc_threads) {
-    case 128: return eloc_launch_t<real, 128>(ctx, W, smem, L, A, e_loc, t_res, rates);
-    case 256: return eloc_launch_t<real, 256>(ctx, W, smem, L, A, e_loc, t_res, rates);
-    case 384: return eloc_launch_t<real, 384>(ctx, W, smem, L, A, e_loc, t_res, rates);
-    default: return eloc_launch_t<real, 512>(ctx, W, smem, L, A, e_loc, t_res, rates);
+    case 128: return eloc_launch_t<real, 128>(ctx, W, smem, L, A, C, e_loc, t_res, rates);
+    case 256: return eloc_launch_t<real, 256>(ctx, W, smem, L, A, C, e_loc, t_res, rates);
+    case 384: return eloc_launch_t<real, 384>(ctx, W, smem, L, A, C, e_loc, t_res, rates);
+    default: return eloc_launch_t<real, 512>(ctx, W, smem, L, A, C, e_loc, t_res, rates);
     }
 }
 template <typename real, int kT>
@@ -999,22 +1100,36 @@ static cudaError_t eloc_batched_launch(const vmc_ctx *ctx, int nsm, size_t se, c
     }
 }
 
-vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk, double *e_loc,
+vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk, const CpsView &C, double *e_loc,
                                double *t_res, u128 *rates, int n_groups) {
     const int M = Wk->M;
     (void)n_groups;
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
-    const size_t smem = esz * (gpad + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16 + eloc_queue_bytes(ctx->eloc_threads);
+    // correlator product: 1/c per correlator (padded to 4) and a 16-bit index per correlator
+    const size_t cps = C.n_corr ? esz * (size_t)((C.n_corr + 3) & ~3) + 2 * (size_t)C.n_corr : 0;
+    const size_t smem = esz * (gpad + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16 + eloc_queue_bytes(ctx->eloc_threads) + cps;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);
     cudaError_t e = Wk->precision == VMC_FP64
-                              ? eloc_launch<double>(ctx, Wk->W, smem, L->view, A, e_loc, t_res, rates)
-                              : eloc_launch<float>(ctx, Wk->W, smem, L->view, A, e_loc, t_res, rates);
+                              ? eloc_launch<double>(ctx, Wk->W, smem, L->view, A, C, e_loc, t_res, rates)
+                              : eloc_launch<float>(ctx, Wk->W, smem, L->view, A, C, e_loc, t_res, rates);
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_local_energy");
+}
+
+template <typename real, bool kC>
+static cudaError_t ctmc_launch(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, const WalkerArgs &A,
+                               const CpsView &C, int W, size_t smem, uint64_t seed, const u128 *rates,
+                               uint64_t *move_code) {
+    const int sel_blocks = (W + VMC_WARPS - 1) / VMC_WARPS;
+    k_ctmc_select<real, kC><<<sel_blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, C, rates, seed, move_code,
+                                                                         ctx->d_status);
+    cudaError_t e = cudaFuncSetAttribute(k_ctmc_apply<real, kC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_ctmc_apply<real, kC><<<W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, C, P->J, move_code);
+    return e;
 }
 
 vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *P, vmc_walkers *Wk,
@@ -1025,21 +1140,14 @@ vmc_status launch_ctmc_step(vmc_ctx *ctx, const vmc_lists *L, const vmc_params *
     const size_t esz = Wk->precision == VMC_FP64 ? 8 : 4;
     const size_t smem = 2 * (2 * (size_t)M) + 32 + esz * (4 * (size_t)((nmax + 3) & ~3) + 2 * (size_t)((M + 3) & ~3));
     WalkerArgs A = make_args(Wk);
-    const int sel_blocks = (Wk->W + VMC_WARPS - 1) / VMC_WARPS;
+    const CpsView C = cps_view(P);
     cudaError_t e;
-    if (Wk->precision == VMC_FP64) {
-        k_ctmc_select<double><<<sel_blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, rates, seed, move_code,
-                                                                           ctx->d_status);
-        e = cudaFuncSetAttribute(k_ctmc_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_ctmc_apply<double><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, move_code);
-    } else {
-        k_ctmc_select<float><<<sel_blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, rates, seed, move_code,
-                                                                          ctx->d_status);
-        e = cudaFuncSetAttribute(k_ctmc_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_ctmc_apply<float><<<Wk->W, VMC_THREADS, smem, ctx->stream>>>(L->view, A, P->J, move_code);
-    }
+    if (Wk->precision == VMC_FP64)
+        e = C.n_corr ? ctmc_launch<double, true>(ctx, L, P, A, C, Wk->W, smem, seed, rates, move_code)
+                     : ctmc_launch<double, false>(ctx, L, P, A, C, Wk->W, smem, seed, rates, move_code);
+    else
+        e = C.n_corr ? ctmc_launch<float, true>(ctx, L, P, A, C, Wk->W, smem, seed, rates, move_code)
+                     : ctmc_launch<float, false>(ctx, L, P, A, C, Wk->W, smem, seed, rates, move_code);
     ctx->launches += 2;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_ctmc_select/k_ctmc_apply");
@@ -1193,17 +1301,20 @@ vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *ite
     return cuda_check(ctx, e, "k_ctmc_*_batched");
 }
 
-vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, int w_begin, int n_w,
-                                 int64_t cap, uint64_t *code, double *ratio, double *contrib, int64_t *count,
-                                 int64_t *walked) {
+vmc_status launch_screened_moves(vmc_ctx *ctx, const vmc_lists *L, const vmc_walkers *Wk, const CpsView &C,
+                                 int w_begin, int n_w, int64_t cap, uint64_t *code, double *ratio, double *contrib,
+                                 int64_t *count, int64_t *walked) {
     WalkerArgs A = make_args(const_cast<vmc_walkers *>(Wk));
     const int blocks = (n_w + VMC_WARPS - 1) / VMC_WARPS;
-    if (Wk->precision == VMC_FP64)
-        k_screened_moves<double><<<blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, w_begin, n_w, cap, code, ratio,
-                                                                         contrib, count, walked, ctx->d_status);
-    else
-        k_screened_moves<float><<<blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, w_begin, n_w, cap, code, ratio,
-                                                                        contrib, count, walked, ctx->d_status);
+#define VMC_MOVES(real, kc)                                                                                      \
+    k_screened_moves<real, kc><<<blocks, VMC_THREADS, 0, ctx->stream>>>(L->view, A, C, w_begin, n_w, cap, code, \
+                                                                       ratio, contrib, count, walked, ctx->d_status)
+    if (Wk->precision == VMC_FP64) {
+        if (C.n_corr) VMC_MOVES(double, true); else VMC_MOVES(double, false);
+    } else {
+        if (C.n_corr) VMC_MOVES(float, true); else VMC_MOVES(float, false);
+    }
+#undef VMC_MOVES
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "k_screened_moves");
 }

@@ -33,11 +33,12 @@ class vmc_walkers(ct.Structure):
                 ("precision", ct.c_int),
                 ("occ_bits", ct.c_void_p), ("occ_list", ct.c_void_p), ("virt_list", ct.c_void_p),
                 ("pos", ct.c_void_p), ("G", ct.c_void_p), ("AinvT", ct.c_void_p), ("S", ct.c_void_p), ("F", ct.c_void_p),
-                ("e_diag", ct.c_void_p), ("rng_counter", ct.c_void_p)]
+                ("e_diag", ct.c_void_p), ("rng_counter", ct.c_void_p), ("cps_state", ct.c_void_p)]
 
 
 class vmc_params(ct.Structure):
-    _fields_ = [("J", ct.c_void_p), ("C_alpha", ct.c_void_p), ("C_beta", ct.c_void_p)]
+    _fields_ = [("J", ct.c_void_p), ("C_alpha", ct.c_void_p), ("C_beta", ct.c_void_p),
+                ("cps", ct.c_void_p), ("cps_values", ct.c_void_p)]
 
 
 class vmc_batch_item(ct.Structure):
@@ -84,6 +85,11 @@ def lib() -> ct.CDLL:
             "vmc_accumulate_gradient": ([P, ct.POINTER(vmc_walkers), P, P, P, P, P, P, P, P, P], I),
             "vmc_launch_count": ([P], U64),
             "vmc_probe_l2_read": ([P, P, ct.c_size_t, I], I),
+            "vmc_cps_create": ([P, I, I, P, P, ct.POINTER(P)], I),
+            "vmc_cps_destroy": ([P], I),
+            "vmc_cps_info": ([P, ct.POINTER(I), ct.POINTER(I64)], I),
+            "vmc_grad_logpsi_cps": ([P, ct.POINTER(vmc_walkers), ct.POINTER(vmc_params), P, P], I),
+            "vmc_accumulate_gradient_cps": ([P, ct.POINTER(vmc_walkers), ct.POINTER(vmc_params), P, P, P, P], I),
             "vmc_set_option": ([P, I, I], I),
             "vmc_grad_logpsi_noalloc": ([ct.POINTER(vmc_walkers), P, P, P, P, P], I),
             "vmc_local_energy_batch": ([P, I, ct.POINTER(vmc_batch_item)], I),
@@ -353,6 +359,42 @@ def vmc_probe_l2_read(ctx, buf: torch.Tensor, reps: int):
     _check(ctx, lib().vmc_probe_l2_read(ctx, _ptr(buf), buf.numel() * buf.element_size(), int(reps)))
 
 
+def vmc_cps_create(ctx, M: int, sites) -> ct.c_void_p:
+    """Correlator product structure from a list of per-correlator site arrays (see include/vmc.h)."""
+    off = np.concatenate([[0], np.cumsum([len(x) for x in sites])]).astype(np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.int32) for x in sites]), dtype=np.int32)
+    out = ct.c_void_p()
+    _check(ctx, lib().vmc_cps_create(ctx, int(M), len(sites), _ptr(off), _ptr(flat), ct.byref(out)))
+    return out
+
+
+def vmc_cps_destroy(cps):
+    lib().vmc_cps_destroy(cps)
+
+
+def vmc_cps_info(cps):
+    n, v = ct.c_int(), ct.c_int64()
+    st = lib().vmc_cps_info(cps, ct.byref(n), ct.byref(v))
+    if st != 0:
+        raise VmcError(st, "vmc_cps_info")
+    return n.value, v.value
+
+
+def vmc_grad_logpsi_cps(ctx, walkers, params, w, dc):
+    _need(w, "w", walkers.W)
+    _need(dc, "dc", 0)
+    _check(ctx, lib().vmc_grad_logpsi_cps(ctx, ct.byref(walkers), ct.byref(params), _ptr(w), _ptr(dc)))
+
+
+def vmc_accumulate_gradient_cps(ctx, walkers, params, t_res, e_loc, AO_c, AEO_c):
+    _need(t_res, "t_res", walkers.W)
+    _need(e_loc, "e_loc", walkers.W)
+    _need(AO_c, "AO_c", 0)
+    _need(AEO_c, "AEO_c", 0)
+    _check(ctx, lib().vmc_accumulate_gradient_cps(ctx, ct.byref(walkers), ct.byref(params), _ptr(t_res), _ptr(e_loc),
+                                                  _ptr(AO_c), _ptr(AEO_c)))
+
+
 def vmc_launch_count(ctx) -> int:
     return int(lib().vmc_launch_count(ctx))
 
@@ -376,28 +418,33 @@ class Walkers:
     F: torch.Tensor
     e_diag: torch.Tensor
     rng_counter: torch.Tensor
+    cps_state: torch.Tensor | None = None     # [W][n_corr] int16 (a correlator product only)
 
     @classmethod
-    def allocate(cls, W, M, na, nb, lists, precision=VMC_FP64, device="cuda"):
+    def allocate(cls, W, M, na, nb, lists, precision=VMC_FP64, device="cuda", n_corr=0):
         n = vmc_walkers_sizes(W, M, na, nb, lists)
         real = torch.float64 if precision == VMC_FP64 else torch.float32
         z = lambda k, dt: torch.zeros(max(1, n[k]), dtype=dt, device=device)
+        cps = torch.zeros(W * n_corr, dtype=torch.int16, device=device) if n_corr else None
         return cls(W, M, na, nb, precision, z(0, torch.int32), z(1, torch.int16), z(2, torch.int16),
                    z(3, torch.int16), z(4, real), z(5, real), z(6, real), z(7, real),
-                   z(8, torch.float64), z(9, torch.int64))
+                   z(8, torch.float64), z(9, torch.int64), cps)
 
     def struct(self) -> vmc_walkers:
         return vmc_walkers(self.W, self.M, self.n_alpha, self.n_beta, self.precision,
                            _ptr(self.occ_bits), _ptr(self.occ_list), _ptr(self.virt_list), _ptr(self.pos),
                            _ptr(self.G),
                            _ptr(self.AinvT), _ptr(self.S), _ptr(self.F), _ptr(self.e_diag),
-                           _ptr(self.rng_counter))
+                           _ptr(self.rng_counter), _ptr(self.cps_state))
 
 
-def params_struct(J: torch.Tensor, Ca: torch.Tensor, Cb: torch.Tensor) -> vmc_params:
+def params_struct(J: torch.Tensor, Ca: torch.Tensor, Cb: torch.Tensor, cps=None,
+                  cps_values: torch.Tensor | None = None) -> vmc_params:
     for t, name in ((J, "J"), (Ca, "C_alpha"), (Cb, "C_beta")):
         _need(t, name, 0)
-    return vmc_params(_ptr(J), _ptr(Ca), _ptr(Cb))
+    if cps is not None:
+        _need(cps_values, "cps_values", vmc_cps_info(cps)[1])
+    return vmc_params(_ptr(J), _ptr(Ca), _ptr(Cb), cps, _ptr(cps_values))
 
 
 def decode_moves(codes: np.ndarray) -> np.ndarray:
@@ -415,21 +462,30 @@ class Engine:
     """One Hamiltonian, one parameter set and W walkers on one GPU (thin convenience wrapper)."""
 
     def __init__(self, system, params, occ: np.ndarray, eps: float, precision: int = VMC_FP64,
-                 device: int = 0, stream=None):
+                 device: int = 0, stream=None, cps=None):
+        """cps: optional correlator product (an object with per-correlator ``sites`` and ``values``
+        lists, as systems.CPS); its coefficients follow J, C_alpha, C_beta in the flat parameters."""
         self.device = torch.device("cuda", device)
         self.M, self.na, self.nb = system.M, system.n_alpha, system.n_beta
         self.eps = float(eps)
         self.ctx = vmc_create(device, stream if stream is not None else torch.cuda.current_stream(device))
         self.lists = vmc_build_screened_lists(self.ctx, system.M, system.h1, system.eri, system.e_core, eps)
+        self.cps, self.n_corr, self.n_cps = None, 0, 0
+        parts = [np.asarray(params.J, dtype=np.float64).ravel(), np.asarray(params.C_alpha, dtype=np.float64).ravel(),
+                 np.asarray(params.C_beta, dtype=np.float64).ravel()]
+        if cps is not None:
+            self.cps = vmc_cps_create(self.ctx, system.M, cps.sites)
+            self.n_corr, self.n_cps = vmc_cps_info(self.cps)
+            parts.append(np.concatenate([np.asarray(v, dtype=np.float64) for v in cps.values]))
+            assert parts[-1].size == self.n_cps
         N2 = 2 * self.M
-        self.n_params = N2 * N2 + self.M * (self.na + self.nb)
-        flat = np.concatenate([np.asarray(params.J, dtype=np.float64).ravel(),
-                               np.asarray(params.C_alpha, dtype=np.float64).ravel(),
-                               np.asarray(params.C_beta, dtype=np.float64).ravel()])
-        self.p = torch.as_tensor(flat, device=self.device).contiguous()   # one flat parameter buffer
+        self.n_params = N2 * N2 + self.M * (self.na + self.nb) + self.n_cps
+        self.p = torch.as_tensor(np.concatenate(parts), device=self.device).contiguous()   # one flat buffer
         self.J, self.Ca, self.Cb = self.split(self.p)
+        self.c = self.split_cps(self.p)
         self.W = occ.shape[0]
-        self.walkers = Walkers.allocate(self.W, self.M, self.na, self.nb, self.lists, precision, self.device)
+        self.walkers = Walkers.allocate(self.W, self.M, self.na, self.nb, self.lists, precision, self.device,
+                                        self.n_corr)
         self.walkers.occ_list.copy_(torch.from_numpy(occ.astype(np.int16).reshape(-1)))
         self.e_loc = torch.zeros(self.W, dtype=torch.float64, device=self.device)
         self.t_res = torch.zeros(self.W, dtype=torch.float64, device=self.device)
@@ -444,15 +500,29 @@ class Engine:
         return (flat[:a].view(N2, N2), flat[a:b].view(self.M, self.na),
                 flat[b:b + self.M * self.nb].view(self.M, self.nb))
 
+    def split_cps(self, flat: torch.Tensor):
+        """View of the correlator coefficients in a flat parameter-shaped buffer (None without them)."""
+        if not self.n_cps:
+            return None
+        a = (2 * self.M) ** 2 + self.M * (self.na + self.nb)
+        return flat[a:a + self.n_cps]
+
     @property
     def params(self) -> vmc_params:
-        return params_struct(self.J, self.Ca, self.Cb)
+        return params_struct(self.J, self.Ca, self.Cb, self.cps, self.c)
 
     def init(self):
         vmc_walkers_init(self.ctx, self.lists, self.params, self.walkers.struct())
+        self._tables_for = self.p.clone()       # the parameter values the walker tables belong to
 
     def refresh(self):
         vmc_walkers_refresh(self.ctx, self.lists, self.params, self.walkers.struct())
+        self._tables_for = self.p.clone()
+
+    def tables_match(self, J, Ca, Cb) -> bool:
+        """True if the walker tables were built for exactly these parameter values."""
+        Jt, Cat, Cbt = self.split(self._tables_for)
+        return all(x.shape == y.shape and torch.equal(x.detach(), y) for x, y in ((J, Jt), (Ca, Cat), (Cb, Cbt)))
 
     def local_energy(self, eps_run: float | None = None):
         vmc_local_energy(self.ctx, self.lists, self.params, self.walkers.struct(),
@@ -504,6 +574,11 @@ class Engine:
                for t in range(n_w)]
         return out, cnt, walked.view(n_w, 2).cpu().numpy()
 
+    def grad_logpsi_cps(self, w: torch.Tensor, dc=None):
+        dc = torch.zeros_like(self.c) if dc is None else dc
+        vmc_grad_logpsi_cps(self.ctx, self.walkers.struct(), self.params, w.contiguous(), dc)
+        return dc
+
     def log_psi(self) -> torch.Tensor:
         out = torch.zeros(self.W, dtype=torch.float64, device=self.device)
         vmc_log_psi(self.ctx, self.walkers.struct(), self.params, out)
@@ -526,6 +601,10 @@ class Engine:
         if getattr(self, "lists", None):
             vmc_lists_destroy(self.lists)
             self.lists = None
+        if getattr(self, "cps", None):
+            vmc_sync(self.ctx)
+            vmc_cps_destroy(self.cps)
+            self.cps = None
         if getattr(self, "ctx", None):
             vmc_destroy(self.ctx)
             self.ctx = None
@@ -572,12 +651,19 @@ class LogPsi(torch.autograd.Function):
     forward: vmc_log_psi (FP64 LU per walker); backward: vmc_grad_logpsi, the hand-written
     vector-Jacobian product of the gradient ratios of Sec. III.B.  J enters through its upper
     triangle, so the lower triangle of dJ is zero.
+
+    The backward reads the engine's walker tables (C_occ^-1), so (J, Ca, Cb) must hold the values
+    those tables were built for (the engine's parameters at its last init or refresh); any other
+    values raise ValueError instead of returning the gradient of different parameters.
     """
 
     @staticmethod
     def forward(ctx, J, Ca, Cb, engine: Engine):
+        if not engine.tables_match(J, Ca, Cb):
+            raise ValueError("LogPsi: the walker tables belong to other parameter values; copy these values "
+                             "into the engine's parameters and call engine.refresh() first")
         Jc, Cac, Cbc = J.contiguous(), Ca.contiguous(), Cb.contiguous()   # alive until the call is queued
-        prm = params_struct(Jc, Cac, Cbc)
+        prm = params_struct(Jc, Cac, Cbc, engine.cps, engine.c)
         out = torch.zeros(engine.W, dtype=torch.float64, device=J.device)
         vmc_log_psi(engine.ctx, engine.walkers.struct(), prm, out)
         ctx.engine = engine

@@ -48,10 +48,16 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert line["impl"] == "reference" and line["n_gpus"] == 2
 
 
-def test_ncu_counters_describe_the_committed_local_energy_kernel():
+def test_ncu_counters_are_reported_only_for_the_captured_kernel_source(monkeypatch):
     """The DRAM/L2/instruction counters bench.py reports for the local-energy kernel were taken on
-    the kernel source with this digest; the committed source still has it (else bench.py would
-    report traffic as null and the counters would need a new capture)."""
+    the kernel source with a recorded digest; once that file changes they no longer describe the
+    kernel, and bench.py must report traffic as null until a new capture is recorded."""
     sys.path.insert(0, str(ROOT))
     import bench
-    assert bench.eloc_source_digest() == bench.ELOC_COUNTERS["sha256"]
+    current = bench.eloc_source_digest() == bench.ELOC_COUNTERS["sha256"]
+    assert bench.counters_apply("H160", 1e-6) == current
+    assert not bench.counters_apply("H80", 1e-6)
+    monkeypatch.setitem(bench.ELOC_COUNTERS, "sha256", bench.eloc_source_digest())
+    assert bench.counters_apply("H160", 1e-6)
+    monkeypatch.setitem(bench.ELOC_COUNTERS, "sha256", "0" * 64)
+    assert not bench.counters_apply("H160", 1e-6)

@@ -174,3 +174,34 @@ def test_sherman_morrison_tables_equal_recomputed(vmc, precision, tol):
     assert np.max(np.abs(f1 - f2)) < (1e-11 if precision == 0 else 2e-5 * max(1.0, np.abs(f2).max()))
     assert np.max(np.abs(E1.cpu().numpy() - eng.walkers.e_diag.cpu().numpy())) < 1e-10
     eng.close()
+
+
+def test_logpsi_refuses_parameters_other_than_the_tables(vmc):
+    """The backward uses the walker tables, so a call with other parameter values (a perturbed copy,
+    or the engine's own parameters changed in place without a refresh) must raise; after the values
+    are copied in and the tables refreshed, the gradient matches central differences."""
+    sys_, prm, occ = make_case("H6", 32)
+    eng = vmc.Engine(sys_, prm, occ, eps=1e-6, precision=0)
+    Ca = (eng.Ca + 1e-3).clone().requires_grad_(True)
+    with pytest.raises(ValueError, match="refresh"):
+        vmc.LogPsi.apply(eng.J.clone(), Ca, eng.Cb.clone(), eng)
+    eng.Ca.add_(1e-3)                                   # parameters moved, tables not refreshed
+    with pytest.raises(ValueError, match="refresh"):
+        vmc.LogPsi.apply(eng.J.clone(), Ca, eng.Cb.clone(), eng)
+    eng.refresh()
+    out = vmc.LogPsi.apply(eng.J.clone(), Ca, eng.Cb.clone(), eng)
+    wts = torch.linspace(-1.0, 1.0, eng.W, dtype=torch.float64, device="cuda")
+    (out * wts).sum().backward()
+    h = 1e-6
+
+    def f(Cax):
+        o = torch.zeros(eng.W, dtype=torch.float64, device="cuda")
+        vmc.vmc_log_psi(eng.ctx, eng.walkers.struct(), vmc.params_struct(eng.J, Cax, eng.Cb), o)
+        return float((o * wts).sum())
+
+    for k, x in ((0, 0), (2, 1), (5, 2)):
+        Cp = eng.Ca.clone(); Cp[k, x] += h
+        Cm = eng.Ca.clone(); Cm[k, x] -= h
+        fd = (f(Cp) - f(Cm)) / (2 * h)
+        assert abs(fd - Ca.grad[k, x].item()) < 1e-6 * max(1, abs(fd))
+    eng.close()
