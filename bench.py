@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--walkers", type=int, default=32768)
     ap.add_argument("--sweeps", type=int, default=8, help="CTMC sweeps per optimisation iteration")
     ap.add_argument("--eps", type=float, default=1e-6)
-    ap.add_argument("--forms", default="mixed,fp64,mixed_gj32",
+    ap.add_argument("--forms", default="mixed,fp64,mixed_gj32,mixed_cps",
                     help="mixed: FP32 tables, FP64 LU of C_occ at every refresh; fp64: FP64 throughout; "
-                         "mixed_gj32: FP32 tables, FP32 Gauss-Jordan refresh")
+                         "mixed_gj32: FP32 tables, FP32 Gauss-Jordan refresh; mixed_cps: the mixed form with "
+                         "5-site correlators on every site multiplying the wavefunction (Sec. III.A)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="walkers in the oracle sample (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=S.MASTER_SEED)
@@ -63,8 +64,8 @@ def parse():
     ap.add_argument("--eps-sweep", default="", help="comma-separated eps values: run the eps / size study "
                     "(cost per 1000 samples of H chains) instead of the benchmark")
     ap.add_argument("--study-systems", default="H20,H40,H80,H160")
-    ap.add_argument("--repeats", type=int, default=3,
-                    help="timed loops of K steps (each followed by an end-to-end loop); the median is reported")
+    ap.add_argument("--repeats", type=int, default=4,
+                    help="pairs of timed loops of K steps (device-timed and end to end); medians are reported")
     return ap.parse_args()
 
 
@@ -187,7 +188,7 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------- our arm
-def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
+def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False, cps=None):
     import torch
     from paper_1807_10633_gb300 import vmc
 
@@ -197,7 +198,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
     stream = torch.cuda.Stream(dev)               # every library call of the step runs here
     stream.wait_stream(torch.cuda.current_stream(dev))
     torch.cuda.set_stream(stream)
-    eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=dev.index, stream=stream)
+    eng = vmc.Engine(sys_, prm, occ, eps=args.eps, precision=precision, device=dev.index, stream=stream, cps=cps)
     if args.g_cuda_cores:
         vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, 0)
     if args.grad_j_int:
@@ -217,6 +218,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
     m1 = torch.zeros(np_, **f64)
     m2 = torch.zeros(np_, **f64)
     AOv, AEOv = eng.split(AO), eng.split(AEO)
+    AOc, AEOc = eng.split_cps(AO), eng.split_cps(AEO)     # correlator coefficients (None without them)
     ws = eng.walkers.struct()
     prm_s = eng.params
     # host buffers for the end-to-end variant (pinned)
@@ -238,6 +240,8 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
                 b.record(stream)
                 ev_pairs.append((a, b))
             vmc.vmc_accumulate_gradient(eng.ctx, ws, eng.t_res, eng.e_loc, AOv, AEOv, sums)
+            if AOc is not None:
+                vmc.vmc_accumulate_gradient_cps(eng.ctx, ws, prm_s, eng.t_res, eng.e_loc, AOc, AEOc)
             vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm_s, ws, D.rank_seed(seed + it, rank), eng.moves)
 
     def update():
@@ -323,10 +327,14 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False):
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
     dev_ms, e2e_ms = [], []
-    for r in range(args.repeats):                # device-timed and end-to-end loops interleaved
-        ms_r, launches = timed_loop(e2e=False, it0=1000 + 2 * r * args.steps)
-        dev_ms.append(ms_r)
-        e2e_ms.append(timed_loop(e2e=True, it0=1000 + (2 * r + 1) * args.steps)[0])
+    # device-timed and end-to-end loops in the order d e | e d | d e | ...: every step moves the
+    # parameters, so the workload drifts slowly; this order gives both arms the same mean position
+    for r in range(args.repeats):
+        for k, e2e in enumerate((False, True) if r % 2 == 0 else (True, False)):
+            ms_r, launches_r = timed_loop(e2e=e2e, it0=1000 + (2 * r + k) * args.steps)
+            (e2e_ms if e2e else dev_ms).append(ms_r)
+            if not e2e:
+                launches = launches_r
     clk = clocks.stop()
     vmc.vmc_sync(eng.ctx)
     ms, ms_e2e = statistics.median(dev_ms), statistics.median(e2e_ms)
@@ -595,8 +603,9 @@ def main():
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     results = {}
     for f in forms:
+        cps = S.make_cps(sys_, seed=args.seed + 7, noise=0.05) if f.endswith("_cps") else None
         results[f] = run_form(args, sys_, prm, occ, vmc.VMC_FP64 if f == "fp64" else vmc.VMC_MIXED, rank, world,
-                              gj32=(f == "mixed_gj32"))
+                              gj32=(f == "mixed_gj32"), cps=cps)
     head = results.get("mixed") or results[forms[0]]
     peak, peak_kind = measured_peaks()
     counters_ok = "mixed" in results and counters_apply(args.system, args.eps)
@@ -646,6 +655,7 @@ def main():
     for f, r in results.items():
         if f != "mixed" or len(results) == 1:
             line[f"{f}_form"] = {"value": r["value"] * scale, "ms_per_step": r["ms_per_step"],
+                                 "n_params": r["n_params"],
                                  "eloc_ms": r["eloc_ms"], "eloc_gbs": r["eloc_gbs"],
                                  "e2e_value": r["e2e_value"] * scale, "repeats": r["repeats"],
                                  "energy_per_electron": r["energy"] / sys_.n_elec}
@@ -657,7 +667,7 @@ def main():
         line["mixed_error"] = {f: {"max_mEh_per_electron": float(np.max(np.abs(r["e_start"] - ref))) * 1e3 / sys_.n_elec,
                                    "mean_mEh_per_electron": float(np.mean(np.abs(r["e_start"] - ref))) * 1e3 / sys_.n_elec,
                                    "walkers": int(ref.size), "against": "FP64 form on the GPU, same determinants"}
-                               for f, r in results.items() if f != "fp64"}
+                               for f, r in results.items() if f != "fp64" and not f.endswith("_cps")}
     if not args.no_batch:
         line["batched_uneven"] = run_batch(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -667,7 +677,7 @@ def main():
         cb["parity_sample"] = {f: (float(np.max(np.abs(r["e_start"][:sample] - el_orc) / np.maximum(1.0, np.abs(el_orc))))
                                    if f == "fp64" else
                                    float(np.max(np.abs(r["e_start"][:sample] - el_orc))) * 1e3 / sys_.n_elec)
-                               for f, r in results.items()}
+                               for f, r in results.items() if not f.endswith("_cps")}
         cb["parity_sample_units"] = "fp64: max relative E_L error; mixed forms: max mEh per electron"
         line["cpu_baseline"] = cb
     if rank == 0:

@@ -76,6 +76,7 @@ __global__ void k_cps_invmax(CpsView C, int W, const uint16_t *__restrict__ stat
     const int64_t tot = (int64_t)W * C.n_corr;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(t % C.n_corr);
+        if (state[t] >= C.val_off[l + 1] - C.val_off[l]) continue;   // inconsistent state: never read
         m = fmax(m, 1.0 / fabs(C.values[C.val_off[l] + state[t]]));
     }
 #pragma unroll
@@ -115,6 +116,7 @@ __global__ void k_cps_grad(CpsView C, int W, const uint16_t *__restrict__ state,
     const int s0 = sexp[0], s1 = sexp[1];
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < tot; x += (int64_t)gridDim.x * blockDim.x) {
         const int w = (int)(x / C.n_corr), l = (int)(x % C.n_corr);
+        if (state[x] >= C.val_off[l + 1] - C.val_off[l]) continue;   // inconsistent state: never read
         const int64_t k = C.val_off[l] + state[x];
         const double inv = 1.0 / C.values[k];
         const long long q0 = __double2ll_rn(scalbn(cps_weight(0, t, e, w) * inv, s0));
