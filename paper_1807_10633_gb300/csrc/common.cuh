@@ -80,6 +80,10 @@ struct ListsView {
     // diagonal tables: Jd[p][q] = (pp|qq), Kd[p][q] = (pq|qp); hd[p] = h_pp; h1 full
     const double *Jd, *Kd, *hd, *h1;
     double e_core;
+    // work units of the local energy, [n_groups][32] in canonical order: {key naming the unit's own
+    // orbitals (a | b << 16, spatial for kinds 0-1, alpha | beta << 16 for kind 2), list base,
+    // list length at the current eps_run (0: no unit), kind | spin << 2}
+    const uint4 *unit_tab;
 };
 
 // Correlator product (Sec. III.A): device view of the structure plus the coefficient table.
@@ -87,18 +91,20 @@ struct ListsView {
 #define VMC_CPS_MAX_PER_SITE 16    // correlators covering one site
 struct CpsView {
     int n_corr;                    // 0: no correlator product
+    int M, nnz;                    // orbitals; total sites over the correlators (= site_ent entries)
     const int32_t *corr_off;       // [n_corr + 1]: sites of correlator l are corr_sites[corr_off[l] ..)
     const int32_t *corr_sites;
-    const int64_t *val_off;        // [n_corr + 1]: coefficients of l at values[val_off[l] ..], 4^k of them
+    const int32_t *val_off;        // [n_corr + 1]: coefficients of l at values[val_off[l] ..], 4^k of them
     const int32_t *site_off;       // [M + 1]: correlators covering site k are site_ent[site_off[k] ..)
     const uint32_t *site_ent;      // (l << 16) | 4^t, t = the site's digit position in l; l ascending
     const double *values;          // the coefficients (parameters), FP64, device
+    const float *values32;         // FP32 copy made by the last walker (re)initialisation (mixed form)
 };
 
 struct vmc_cps {
-    int M = 0, n_corr = 0;
+    int M = 0, n_corr = 0, nnz = 0;
     int64_t n_values = 0;
-    void *dev = nullptr;           // one device allocation: offsets, sites, site table
+    void *dev = nullptr;           // one device allocation: offsets, sites, site table, FP32 copy
     CpsView view{};                // values == nullptr (passed with the parameters)
 };
 

@@ -136,6 +136,11 @@ __global__ void k_cps_finish(int64_t n_values, int n_out, const unsigned long lo
     }
 }
 
+__global__ void k_cps_convert(int64_t n, const double *__restrict__ v, float *__restrict__ v32) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        v32[k] = (float)v[k];
+}
+
 int grid_for(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
@@ -165,7 +170,9 @@ vmc_status launch_cps_state(vmc_ctx *ctx, const vmc_params *P, vmc_walkers *Wk) 
     if (!C.n_corr) return VMC_OK;
     k_cps_state<<<grid_for((int64_t)Wk->W * C.n_corr), 256, 0, ctx->stream>>>(C, Wk->W, Wk->M, Wk->occ_bits,
                                                                               Wk->cps_state);
-    ctx->launches += 1;
+    const int64_t nv = P->cps->n_values;
+    k_cps_convert<<<grid_for(nv), 256, 0, ctx->stream>>>(nv, C.values, (float *)C.values32);
+    ctx->launches += 2;
     return cuda_check(ctx, cudaGetLastError(), "k_cps_state");
 }
 
@@ -208,7 +215,7 @@ vmc_status vmc_cps_create(vmc_ctx *ctx, int M, int n_corr, const int32_t *h_off,
     if (M < 1 || M > VMC_MAX_M) return set_err(ctx, VMC_ERR_ARG, "M must be in [1, 256]");
     if (n_corr < 1 || n_corr > 65534) return set_err(ctx, VMC_ERR_ARG, "n_corr must be in [1, 65534]");
     if (h_off[0] != 0) return set_err(ctx, VMC_ERR_ARG, "h_off[0] must be 0");
-    std::vector<int64_t> val_off(n_corr + 1, 0);
+    std::vector<int32_t> val_off(n_corr + 1, 0);
     std::vector<std::vector<uint32_t>> per_site(M);
     for (int l = 0; l < n_corr; ++l) {
         const int k = h_off[l + 1] - h_off[l];
@@ -220,7 +227,9 @@ vmc_status vmc_cps_create(vmc_ctx *ctx, int M, int n_corr, const int32_t *h_off,
                 if (h_sites[h_off[l] + u] == site) return set_err(ctx, VMC_ERR_ARG, "repeated site in a correlator");
             per_site[site].push_back(((uint32_t)l << 16) | (1u << (2 * t)));
         }
-        val_off[l + 1] = val_off[l] + ((int64_t)1 << (2 * k));
+        if ((int64_t)val_off[l] + ((int64_t)1 << (2 * k)) > 0x7FFFFFFF)
+            return set_err(ctx, VMC_ERR_ARG, "more than 2^31 - 1 coefficients");
+        val_off[l + 1] = val_off[l] + (1 << (2 * k));
     }
     std::vector<int32_t> site_off(M + 1, 0);
     std::vector<uint32_t> site_ent;
@@ -235,17 +244,19 @@ vmc_status vmc_cps_create(vmc_ctx *ctx, int M, int n_corr, const int32_t *h_off,
     c->M = M;
     c->n_corr = n_corr;
     c->n_values = val_off[n_corr];
+    c->nnz = (int)nnz;
     size_t o_off = 0, o_sites = align256(o_off + sizeof(int32_t) * (n_corr + 1));
     size_t o_val = align256(o_sites + sizeof(int32_t) * nnz);
-    size_t o_soff = align256(o_val + sizeof(int64_t) * (n_corr + 1));
+    size_t o_soff = align256(o_val + sizeof(int32_t) * (n_corr + 1));
     size_t o_ent = align256(o_soff + sizeof(int32_t) * (M + 1));
-    size_t total = align256(o_ent + sizeof(uint32_t) * (site_ent.size() + 1));
+    size_t o_v32 = align256(o_ent + sizeof(uint32_t) * (site_ent.size() + 1));
+    size_t total = align256(o_v32 + sizeof(float) * (size_t)c->n_values);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->dev, total);
     char *b = (char *)c->dev;
     if (e == cudaSuccess) e = cudaMemcpy(b + o_off, h_off, sizeof(int32_t) * (n_corr + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_sites, h_sites, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + o_val, val_off.data(), sizeof(int64_t) * (n_corr + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_val, val_off.data(), sizeof(int32_t) * (n_corr + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_soff, site_off.data(), sizeof(int32_t) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !site_ent.empty())
         e = cudaMemcpy(b + o_ent, site_ent.data(), sizeof(uint32_t) * site_ent.size(), cudaMemcpyHostToDevice);
@@ -255,9 +266,12 @@ vmc_status vmc_cps_create(vmc_ctx *ctx, int M, int n_corr, const int32_t *h_off,
     }
     CpsView &v = c->view;
     v.n_corr = n_corr;
+    v.M = M;
+    v.nnz = (int)nnz;
     v.corr_off = (const int32_t *)(b + o_off);
     v.corr_sites = (const int32_t *)(b + o_sites);
-    v.val_off = (const int64_t *)(b + o_val);
+    v.val_off = (const int32_t *)(b + o_val);
+    v.values32 = (const float *)(b + o_v32);
     v.site_off = (const int32_t *)(b + o_soff);
     v.site_ent = (const uint32_t *)(b + o_ent);
     v.values = nullptr;

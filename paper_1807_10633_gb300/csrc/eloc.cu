@@ -130,6 +130,7 @@ struct Unit {
     int cls;       // spin for kinds 0 and 1
     int ci, cj;    // columns of i and j
     int i, j;      // spin orbitals
+    uint32_t sent; // key naming the unit's own (occupied) orbitals
     real einv;     // (1/E_i)(1/E_j)   (1/E_i for singles)
 };
 
@@ -147,29 +148,35 @@ struct View {
     const real *S;         // walker S in global (used when E == nullptr)
     const real *F;         // walker F [2][ns_pad]
     CpsView C;             // correlator product (C.n_corr == 0: none)
-    const uint16_t *cidx;  // [n_corr] the walker's correlator indices
+    // its tables, staged in shared memory by the local energy (global otherwise): per-site
+    // correlator lists, coefficient offsets, and per correlator the position of the walker's
+    // current coefficient (cur == nullptr: val_off[l] + cidx[l] from the global indices) and 1/c
+    const int32_t *soff, *voff, *cur;
+    const uint32_t *sent;
+    const uint16_t *cidx;  // [n_corr] the walker's correlator indices (global)
     const real *cinv;      // [n_corr] 1 / c_l[n_l] (shared), or nullptr: from the coefficients
     Geo geo;
-    __device__ real cinv_of(int l) const {
-        return cinv ? cinv[l] : rrcp((real)__ldg(&C.values[__ldg(&C.val_off[l]) + cidx[l]]));
-    }
+    __device__ int cur_of(int l) const { return cur ? cur[l] : voff[l] + (int)cidx[l]; }
+    __device__ real coef(int k) const;
+    __device__ real cinv_of(int l) const { return cinv ? cinv[l] : rrcp(coef(cur_of(l))); }
     __device__ real Ev(int p) const { return E ? E[p] : rexp(S[p]); }              // p virtual
     __device__ real Eiv(int p) const { return E ? E[p] : rrcp(rexp(S[p])); }       // p occupied
     __device__ bool occ(int p) const { return !(pos[p] & 0x8000); }
 };
 
-// Candidate j of spin-orbital row i, t-th in ascending order (t < row_ncand).
-__device__ __forceinline__ int row_ncand(const ListsView &L, int i) {
-    const int M = L.M, s = i >= M, p = i - s * M;
-    const int nS = min(L.band, M - 1 - p);
-    if (s) return nS;
-    return nS + (min(M - 1, p + L.band) - max(0, p - L.band) + 1);
-}
-__device__ __forceinline__ int row_cand(const ListsView &L, int i, int t) {
-    const int M = L.M, s = i >= M, p = i - s * M;
-    const int nS = min(L.band, M - 1 - p);
-    if (t < nS) return i + 1 + t;
-    return M + max(0, p - L.band) + (t - nS);
+// Correlator coefficient k in the table precision (the mixed form reads the FP32 copy).
+template <> __device__ __forceinline__ float View<float>::coef(int k) const { return __ldg(&C.values32[k]); }
+template <> __device__ __forceinline__ double View<double>::coef(int k) const { return __ldg(&C.values[k]); }
+
+template <typename real> __device__ __forceinline__ real V0coef(const CpsView &C, int k);
+template <> __device__ __forceinline__ float V0coef<float>(const CpsView &C, int k) { return C.values32[k]; }
+template <> __device__ __forceinline__ double V0coef<double>(const CpsView &C, int k) { return C.values[k]; }
+
+// Point a view's correlator tables at the global copies (the CTMC choice, the move set).
+template <typename real>
+__device__ __forceinline__ void cps_global(View<real> &V, const CpsView &C, const uint16_t *cidx) {
+    V.C = C; V.soff = C.site_off; V.sent = C.site_ent; V.voff = C.val_off; V.cur = nullptr;
+    V.cidx = cidx; V.cinv = nullptr;
 }
 
 // Correlator-product ratio prod_l c_l[n_l + delta_l] / c_l[n_l] of the move that empties spin
@@ -188,9 +195,9 @@ __device__ __forceinline__ real cps_ratio(const View<real> &V, int r0, int a0, i
         const int p = x == 0 ? r0 : (x == 1 ? a0 : (x == 2 ? r1 : a1));
         const int sp = p >= M ? 1 : 0, site = p - sp * M;
         d[x] = ((x & 1) ? 1 : -1) * (1 + sp);
-        h[x] = x < nx ? __ldg(&V.C.site_off[site]) : 0;
-        e[x] = x < nx ? __ldg(&V.C.site_off[site + 1]) : 0;
-        c[x] = h[x] < e[x] ? __ldg(&V.C.site_ent[h[x]]) : 0xFFFFFFFFu;
+        h[x] = x < nx ? V.soff[site] : 0;
+        e[x] = x < nx ? V.soff[site + 1] : 0;
+        c[x] = h[x] < e[x] ? V.sent[h[x]] : 0xFFFFFFFFu;
     }
     real r = real(1);
     for (int it = 0; it < 4 * VMC_CPS_MAX_PER_SITE; ++it) {
@@ -202,68 +209,37 @@ __device__ __forceinline__ real cps_ratio(const View<real> &V, int r0, int a0, i
             if ((c[x] >> 16) == l) {
                 delta += d[x] * (int)(c[x] & 0xFFFFu);
                 ++h[x];
-                c[x] = h[x] < e[x] ? __ldg(&V.C.site_ent[h[x]]) : 0xFFFFFFFFu;
+                c[x] = h[x] < e[x] ? V.sent[h[x]] : 0xFFFFFFFFu;
             }
-        const int64_t base = __ldg(&V.C.val_off[l]);
-        const int idx = (int)V.cidx[l] + delta;
-        if (idx < 0 || idx >= (int)(__ldg(&V.C.val_off[l + 1]) - base)) return real(NAN);
-        r = rmul(r, rmul((real)__ldg(&V.C.values[base + idx]), V.cinv_of((int)l)));
+        const int k = V.cur_of((int)l) + delta;
+        if (k < V.voff[l] || k >= V.voff[l + 1]) return real(NAN);
+        r = rmul(r, rmul(V.coef(k), V.cinv_of((int)l)));
     }
     return r;
 }
 
-// Set up the unit of lane `lane` in group g.  Returns false if the lane has no active unit.
+// Unit of lane `lane` in group g, from the lists' unit table (the static (group, lane) -> (i, j,
+// list) map, with the list lengths of the current eps_run): active if the list is non-empty and i
+// (and j) are occupied in this walker.  Returns false if the lane has no active unit.
 template <typename real>
 __device__ __forceinline__ bool setup_unit(const ListsView &L, const View<real> &V, int g, int lane,
                                            Unit<real> &u) {
-    const int M = L.M, Gs = (2 * M + 31) / 32;
-    u.base = 0; u.len = 0; u.kind = 0; u.cls = 0; u.ci = 0; u.cj = 0; u.i = -1; u.j = -1; u.einv = real(0);
-    if (g < Gs) {
-        const int i = g * 32 + lane;
-        if (i >= 2 * M || !V.occ(i)) return false;
-        const int s = i >= M, pi = i - s * M;
-        u.kind = 0; u.cls = s; u.i = i; u.j = -1;
-        u.base = L.s_off[pi]; u.len = L.s_len[pi];
-        u.ci = V.pos[i]; u.cj = 0;
-        u.einv = V.Eiv(i);
-        return u.len > 0;
-    }
-    // alpha rows: cpr groups each; beta rows: rpg rows per group (lane = row offset * band +
-    // candidate), or cpr_b groups each.  Groups and lanes run in ascending (i, j) order.
-    const int ga = g - Gs;
-    int i, t;
-    if (ga < M * L.cpr) {
-        const int chunk = ga % L.cpr;
-        i = ga / L.cpr;
-        t = chunk * 32 + lane;
-    } else if (L.rpg > 1) {
-        const int ro = lane / L.band;
-        i = M + (ga - M * L.cpr) * L.rpg + ro;
-        t = lane - ro * L.band;
-        if (ro >= L.rpg || i >= 2 * M) return false;
+    const int M = L.M;
+    const uint4 t = __ldg(&L.unit_tab[(size_t)g * 32 + lane]);
+    u.base = t.y; u.len = t.z; u.kind = (int)(t.w & 3); u.cls = (int)(t.w >> 2); u.sent = t.x;
+    u.ci = 0; u.cj = 0; u.einv = real(0);
+    const int lo = (int)(t.x & 0xFFFFu), hi = (int)(t.x >> 16);
+    u.i = u.kind == 2 ? lo : u.cls * M + lo;
+    u.j = u.kind == 0 ? -1 : (u.kind == 2 ? M + hi : u.cls * M + hi);
+    if (u.len == 0 || !V.occ(u.i)) return false;
+    if (u.kind != 0 && !V.occ(u.j)) return false;
+    u.ci = V.pos[u.i];
+    if (u.kind == 0) {
+        u.einv = V.Eiv(u.i);
     } else {
-        const int gb = ga - M * L.cpr, chunk = gb % L.cpr_b;
-        i = M + gb / L.cpr_b;
-        t = chunk * 32 + lane;
+        u.cj = V.pos[u.j];
+        u.einv = rmul(V.Eiv(u.i), V.Eiv(u.j));
     }
-    if (!V.occ(i)) return false;
-    if (t >= row_ncand(L, i)) return false;
-    const int j = row_cand(L, i, t);
-    if (!V.occ(j)) return false;
-    const int si = i >= M, sj = j >= M, pi = i - si * M, pj = j - sj * M;
-    u.i = i; u.j = j;
-    u.ci = V.pos[i]; u.cj = V.pos[j];
-    if (si == sj) {
-        const int tt = tri_index(pi, pj, M);
-        u.kind = 1; u.cls = si;
-        u.base = L.ds_off[tt]; u.len = L.ds_len[tt];
-    } else {
-        const int tt = pi * M + pj;
-        u.kind = 2; u.cls = 0;
-        u.base = L.do_off[tt]; u.len = L.do_len[tt];
-    }
-    if (u.len == 0) return false;
-    u.einv = rmul(V.Eiv(i), V.Eiv(j));
     return true;
 }
 
@@ -402,41 +378,86 @@ __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real>
     }
 }
 
-// Walk the list of one unit of kind K (lanes over entries, 32 per chunk): load the 2- or 4-byte key,
-// test the target orbital(s) in the shared orbital map and queue the free entries; every 32 queued
-// entries are evaluated at once.  Lanes past the end test `sent`, a key naming the unit's own
-// (occupied) orbitals, so the test needs no bounds branch.  pos and the queue are addressed as
-// 32-bit shared-memory addresses.
-template <int K, typename real, typename acc_t, bool kC>
-__device__ __forceinline__ void walk_unit(const ListsView &L, const View<real> &V, uint32_t base, uint32_t len,
-                                          int cls, int src, uint32_t sent, uint32_t *wq, int &q, int lane,
-                                          unsigned lt_mask, int cci, int ccj, real ceinv, int cmeta, int cii, int cjj,
-                                          acc_t &e_grp, u128 &q_grp, unsigned &flag) {
+// Walk the lists of one group's active units, concatenated in lane order (packed walk): each pass
+// reads 32 consecutive entries of the concatenation, one per lane; lane l finds the unit holding
+// flat entry f = c0 + l by a binary search of the inclusive length prefix (incl) over the lanes,
+// loads the entry's 2- or 4-byte key, tests the target orbital(s) in the shared orbital map and
+// queues the free entries (queue 0: singles or same-spin doubles, queue 1: opposite-spin doubles);
+// every 32 queued entries are evaluated at once.  Entry code = list index << 5 | unit lane.  A unit
+// therefore costs no pass of its own: a group's units share passes, the last one partly filled.
+// pos and the queues are addressed as 32-bit shared-memory addresses.
+template <bool kSingles, typename real, typename acc_t, bool kC>
+__device__ __forceinline__ void walk_group(const ListsView &L, const View<real> &V, uint32_t total, uint32_t incl,
+                                           uint32_t cstart, uint32_t cbase, uint32_t csent, int cmeta, uint32_t *wq,
+                                           int lane, unsigned lt_mask, int cci, int ccj, real ceinv, int cii, int cjj,
+                                           acc_t &e_grp, u128 &q_grp, unsigned &flag) {
     const int M = V.geo.M;
-    const uint32_t sA = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? 0 : cls * M));
-    const uint32_t sB = (uint32_t)__cvta_generic_to_shared(V.pos + (K == 2 ? M : cls * M));
-    const uint32_t sQ = (uint32_t)__cvta_generic_to_shared(wq);
-    for (uint32_t k0 = 0; k0 < len; k0 += 32) {
-        const uint32_t idx = base + k0 + lane;
-        uint32_t key = sent;
-        if (k0 + lane < len) key = K == 0 ? (uint32_t)__ldg(&L.s_a[idx]) : __ldg((K == 2 ? L.do_ab : L.ds_ab) + idx);
+    const uint32_t sPos = (uint32_t)__cvta_generic_to_shared(V.pos);
+    const uint32_t sQ0 = (uint32_t)__cvta_generic_to_shared(wq), sQ1 = sQ0 + 256u;
+    int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        const uint32_t f = c0 + lane;
+        int su = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, su + st - 1) <= f) su += st;
+        const uint32_t ub = __shfl_sync(0xffffffffu, cbase, su), us = __shfl_sync(0xffffffffu, cstart, su);
+        const uint32_t usent = __shfl_sync(0xffffffffu, csent, su);
+        const bool valid = f < total;
+        const uint32_t idx = ub + (f - us);
         uint32_t x, y = 0xFFFFu;
-        asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sA + 2u * (key & 0xFFFFu)));
-        if (K != 0) asm("ld.shared.u16 %0, [%1];" : "=r"(y) : "r"(sB + 2u * (key >> 16)));
-        const bool pass = x & y & 0x8000u;
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (pass)
-            asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ + 4u * (uint32_t)(q + __popc(bal & lt_mask))),
-                         "r"((idx << 5) | (uint32_t)src) : "memory");
-        q += __popc(bal);
-        if (q >= 32) {
+        bool p0, p1;
+        if (kSingles) {
+            const int cls = __shfl_sync(0xffffffffu, cmeta, su) >> 2;
+            const uint32_t key = valid ? (uint32_t)__ldg(&L.s_a[idx]) : usent;
+            asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * ((uint32_t)(cls * M) + (key & 0xFFFFu))));
+            p0 = valid && (x & 0x8000u);
+            p1 = false;
+        } else {
+            const int um = __shfl_sync(0xffffffffu, cmeta, su), kind = um & 3, cls = um >> 2;
+            const uint32_t key = valid ? __ldg((kind == 2 ? L.do_ab : L.ds_ab) + idx) : usent;
+            const uint32_t oA = kind == 2 ? 0u : (uint32_t)(cls * M), oB = kind == 2 ? (uint32_t)M : oA;
+            asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * (oA + (key & 0xFFFFu))));
+            asm("ld.shared.u16 %0, [%1];" : "=r"(y) : "r"(sPos + 2u * (oB + (key >> 16))));
+            const bool pass = valid && (x & y & 0x8000u);
+            p0 = pass && kind != 2;
+            p1 = pass && kind == 2;
+        }
+        const unsigned b0 = __ballot_sync(0xffffffffu, p0);
+        const uint32_t code = (idx << 5) | (uint32_t)su;
+        if (p0)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ0 + 4u * (uint32_t)(qn0 + __popc(b0 & lt_mask))), "r"(code)
+                         : "memory");
+        qn0 += __popc(b0);
+        if (!kSingles) {
+            const unsigned b1 = __ballot_sync(0xffffffffu, p1);
+            if (p1)
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ1 + 4u * (uint32_t)(qn1 + __popc(b1 & lt_mask))),
+                             "r"(code) : "memory");
+            qn1 += __popc(b1);
+        }
+        if (qn0 >= 32) {
             __syncwarp();
-            q -= 32;
-            drain_queue<K, real, acc_t, kC>(L, V, wq + q, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
-                                            flag);
+            qn0 -= 32;
+            drain_queue<kSingles ? 0 : 1, real, acc_t, kC>(L, V, wq + qn0, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj,
+                                                            e_grp, q_grp, flag);
+            __syncwarp();
+        }
+        if (!kSingles && qn1 >= 32) {
+            __syncwarp();
+            qn1 -= 32;
+            drain_queue<2, real, acc_t, kC>(L, V, wq + 64 + qn1, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp,
+                                            q_grp, flag);
             __syncwarp();
         }
     }
+    __syncwarp();
+    if (qn0)
+        drain_queue<kSingles ? 0 : 1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp,
+                                                        q_grp, flag);
+    if (!kSingles && qn1)
+        drain_queue<2, real, acc_t, kC>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
+    __syncwarp();
 }
 
 // Local energy of walker w by the whole CTA (any number of warps).  smraw: dynamic shared memory.
@@ -457,9 +478,13 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     double *eg = (double *)(rates + (size_t)A.W * n_groups) + (size_t)w * n_groups;
     // per warp: two queues of 64 entry codes (idx << 5 | unit lane): kinds 0/1, and kind 2
     uint32_t *wq = (uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + warp * 128;
-    // correlator product: 1 / c_l[n_l] and the indices n_l, after the queues
+    // correlator product, after the queues: 1 / c_l[n_l], the current coefficient positions, the
+    // coefficient offsets and the per-site correlator lists
     real *sCinv = (real *)((uint32_t *)(((uintptr_t)(pos + 2 * M) + 15) & ~(uintptr_t)15) + nwarp * 128);
-    uint16_t *sCidx = (uint16_t *)(sCinv + ((C.n_corr + 3) & ~3));
+    int32_t *sCur = (int32_t *)(sCinv + ((C.n_corr + 3) & ~3));
+    int32_t *sVoff = sCur + C.n_corr;
+    int32_t *sSoff = sVoff + C.n_corr + 1;
+    uint32_t *sSent = (uint32_t *)(sSoff + M + 1);
     __shared__ u128 red_q[32];
     __shared__ int next_group;
 
@@ -482,12 +507,16 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
             sE[p] = (ps & 0x8000) ? e : rrcp(e);
             pos[p] = ps;
         }
-        if (kC)
+        if (kC) {
+            for (int l = tid; l <= C.n_corr; l += nt) sVoff[l] = C.val_off[l];
+            for (int k = tid; k <= M; k += nt) sSoff[k] = C.site_off[k];
+            for (int k = tid; k < C.nnz; k += nt) sSent[k] = C.site_ent[k];
             for (int l = tid; l < C.n_corr; l += nt) {
-                const uint16_t k = A.cps[(size_t)w * C.n_corr + l];
-                sCidx[l] = k;
-                sCinv[l] = rrcp((real)C.values[C.val_off[l] + k]);
+                const int k = C.val_off[l] + (int)A.cps[(size_t)w * C.n_corr + l];
+                sCur[l] = k;
+                sCinv[l] = rrcp(V0coef<real>(C, k));
             }
+        }
         if (tid == 0) next_group = nwarp;
     }
     __syncthreads();
@@ -495,7 +524,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     View<real> V;
     V.pos = pos; V.Ga = sGa; V.Gb = sGb; V.lda = lda; V.ldb = ldb;
     V.E = sE; V.S = nullptr; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
-    V.C = C; V.cidx = sCidx; V.cinv = sCinv;
+    V.C = C; V.soff = sSoff; V.sent = sSent; V.voff = sVoff; V.cur = sCur; V.cidx = nullptr; V.cinv = sCinv;
     typedef typename AccT<real>::type acc_t;
     u128 q_tot = 0;
     unsigned flag = 0;
@@ -508,54 +537,30 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
-        unsigned mask = __ballot_sync(0xffffffffu, act);
         const int cmeta = u.kind | (u.cls << 2);
         const int cci = u.ci, ccj = u.cj, cii = u.i, cjj = u.j;
         const real ceinv = u.einv;
         acc_t e_grp = 0;
         u128 q_grp = 0;
-        int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
-        // key naming the unit's own orbitals (occupied): the test of lanes past the end of a list
-        uint32_t csent = 0;
-        if (act) {
-            if (u.kind == 0) csent = (uint32_t)(u.i - u.cls * M);
-            else if (u.kind == 1) csent = (uint32_t)(u.i - u.cls * M) | ((uint32_t)(u.j - u.cls * M) << 16);
-            else csent = (uint32_t)u.i | ((uint32_t)(u.j - M) << 16);
+        // inclusive prefix of the active units' list lengths over the lanes
+        const uint32_t mylen = act ? u.len : 0u;
+        uint32_t incl = mylen;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
         }
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const uint32_t base = __shfl_sync(0xffffffffu, u.base, src), len = __shfl_sync(0xffffffffu, u.len, src);
-            const int m = __shfl_sync(0xffffffffu, cmeta, src), kind = m & 3, cls = m >> 2;
-            const uint32_t sent = __shfl_sync(0xffffffffu, csent, src);
-            if (base + len > list_size(L, kind)) {   // cannot happen: guard, never read
-                flag |= VMC_DEV_INCONSISTENT;
-                continue;
-            }
-            if (kind == 2)
-                walk_unit<2, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq + 64, qn1, lane, lt_mask, cci, ccj,
-                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
-            else if (kind == 1)
-                walk_unit<1, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj,
-                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
-            else
-                walk_unit<0, real, acc_t, kC>(L, V, base, len, cls, src, sent, wq, qn0, lane, lt_mask, cci, ccj,
-                                              ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
+        uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (__ballot_sync(0xffffffffu, act && u.base + u.len > list_size(L, u.kind))) {   // cannot happen: guard
+            flag |= VMC_DEV_INCONSISTENT;
+            total = 0;
         }
-        __syncwarp();
-        // queue 0 holds singles (singles groups) or same-spin doubles (row groups); queue 1 opposite spin
-        if (qn0) {
-            if (g < n_sgl_groups)
-                drain_queue<0, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
-                                                flag);
-            else
-                drain_queue<1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
-                                                flag);
-        }
-        if (qn1)
-            drain_queue<2, real, acc_t, kC>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
-                                            flag);
-        __syncwarp();
+        if (g < n_sgl_groups)
+            walk_group<true, real, acc_t, kC>(L, V, total, incl, incl - mylen, u.base, u.sent, cmeta, wq, lane,
+                                              lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+        else
+            walk_group<false, real, acc_t, kC>(L, V, total, incl, incl - mylen, u.base, u.sent, cmeta, wq, lane,
+                                               lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
         if (lane == 0) {
@@ -679,7 +684,7 @@ __device__ __forceinline__ void select_walker(const ListsView &L, const WalkerAr
         View<real> V;
         V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
         V.E = nullptr; V.S = Sw; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad; V.geo = geo;
-        V.C = C; V.cidx = kC ? A.cps + (size_t)w * C.n_corr : nullptr; V.cinv = nullptr;
+        if (kC) cps_global(V, C, A.cps + (size_t)w * C.n_corr);
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, gsel, lane, u);
         unsigned mask = __ballot_sync(0xffffffffu, act);
@@ -765,7 +770,7 @@ k_screened_moves(ListsView L, WalkerArgs A, CpsView C, int w_begin, int n_w, int
     V.pos = A.pos + (size_t)w * N2; V.Ga = Gw; V.Gb = Gw + geo.g_off(1); V.lda = geo.na; V.ldb = geo.nb;
     V.E = nullptr; V.S = (const real *)A.S + (size_t)w * N2; V.F = (const real *)A.F + (size_t)w * 2 * L.ns_pad;
     V.geo = geo;
-    V.C = C; V.cidx = kC ? A.cps + (size_t)w * C.n_corr : nullptr; V.cinv = nullptr;
+    if (kC) cps_global(V, C, A.cps + (size_t)w * C.n_corr);
     const unsigned lt_mask = (1u << lane) - 1u;
     int64_t cnt = 0, walked_s = 0, walked_d = 0;
     unsigned flag = 0;
@@ -1108,7 +1113,9 @@ vmc_status launch_local_energy(vmc_ctx *ctx, const vmc_lists *L, vmc_walkers *Wk
     const int na = Wk->n_alpha, nb = Wk->n_beta;
     const size_t gpad = (size_t)(M - na) * (na + 1) + (size_t)(M - nb) * (nb + 1);
     // correlator product: 1/c per correlator (padded to 4) and a 16-bit index per correlator
-    const size_t cps = C.n_corr ? esz * (size_t)((C.n_corr + 3) & ~3) + 2 * (size_t)C.n_corr : 0;
+    const size_t cps = C.n_corr ? esz * (size_t)((C.n_corr + 3) & ~3) + 4 * (2 * (size_t)C.n_corr + 1) +
+                                      4 * ((size_t)M + 1) + 4 * (size_t)C.nnz
+                                : 0;
     const size_t smem = esz * (gpad + 2 * (size_t)M) + 2 * (2 * (size_t)M) + 16 + eloc_queue_bytes(ctx->eloc_threads) + cps;
     if (smem > 200 * 1024) return set_err(ctx, VMC_ERR_ARG, "walker G table does not fit in shared memory");
     WalkerArgs A = make_args(Wk);

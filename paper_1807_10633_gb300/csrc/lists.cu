@@ -238,7 +238,64 @@ const char *check_build_args(int M, const double *h1, const double *eri, int eri
 
 }  // namespace
 
-// Effective list lengths for eps_run (host binary searches, one small upload).
+// The local energy's work units, [n_groups][32] in canonical move order.  Groups: singles blocks of
+// 32 spin orbitals (unit = spin orbital i, list = singles(i)); then one group (or cpr chunks of 32
+// candidates) per alpha spin-orbital row i, whose candidates j > i are the same-spin q in
+// (p, p + band] followed by the opposite-spin q in [p - band, p + band]; then beta rows, rpg of them
+// per group (lane = row offset x band + candidate) or cpr_b chunks each.  Groups and lanes run in
+// ascending (i, j) order, which is the canonical order of the CTMC choice.
+static void build_unit_table(const vmc_lists *L, const uint32_t *s_len, const uint32_t *ds_len,
+                             const uint32_t *do_len, std::vector<uint4> &tab) {
+    const ListsView &v = L->view;
+    const int M = L->M, Gs = (2 * M + 31) / 32;
+    tab.assign((size_t)v.n_groups * 32, make_uint4(0, 0, 0, 0));
+    auto ncand = [&](int i) {   // candidates of spin-orbital row i
+        const int sp = i >= M, p = i - sp * M, nS = std::min(v.band, M - 1 - p);
+        return sp ? nS : nS + (std::min(M - 1, p + v.band) - std::max(0, p - v.band) + 1);
+    };
+    auto cand = [&](int i, int t) {
+        const int sp = i >= M, p = i - sp * M, nS = std::min(v.band, M - 1 - p);
+        return t < nS ? i + 1 + t : M + std::max(0, p - v.band) + (t - nS);
+    };
+    for (int g = 0; g < v.n_groups; ++g)
+        for (int lane = 0; lane < 32; ++lane) {
+            uint4 &e = tab[(size_t)g * 32 + lane];
+            if (g < Gs) {
+                const int i = g * 32 + lane;
+                if (i >= 2 * M) continue;
+                const int sp = i >= M, p = i - sp * M;
+                e = make_uint4((uint32_t)p, L->h_s_off[p], s_len[p], (uint32_t)(sp << 2));
+                continue;
+            }
+            const int ga = g - Gs;
+            int i, t;
+            if (ga < M * v.cpr) {
+                i = ga / v.cpr;
+                t = (ga % v.cpr) * 32 + lane;
+            } else if (v.rpg > 1) {
+                const int ro = lane / v.band;
+                i = M + (ga - M * v.cpr) * v.rpg + ro;
+                t = lane - ro * v.band;
+                if (ro >= v.rpg || i >= 2 * M) continue;
+            } else {
+                const int gb = ga - M * v.cpr;
+                i = M + gb / v.cpr_b;
+                t = (gb % v.cpr_b) * 32 + lane;
+            }
+            if (t >= ncand(i)) continue;
+            const int j = cand(i, t);
+            const int si = i >= M, sj = j >= M, pi = i - si * M, pj = j - sj * M;
+            if (si == sj) {
+                const int tt = tri_index(pi, pj, M);
+                e = make_uint4((uint32_t)pi | ((uint32_t)pj << 16), L->h_ds_off[tt], ds_len[tt], (uint32_t)(1 | (si << 2)));
+            } else {
+                const int tt = pi * M + pj;
+                e = make_uint4((uint32_t)pi | ((uint32_t)pj << 16), L->h_do_off[tt], do_len[tt], 2u);
+            }
+        }
+}
+
+// Effective list lengths for eps_run (host binary searches, one small upload) and the unit table.
 vmc_status lists_set_eps(vmc_ctx *ctx, vmc_lists *L, double eps_run) {
     if (L->eps_run == eps_run) return VMC_OK;
     const int M = L->M;
@@ -250,8 +307,13 @@ vmc_status lists_set_eps(vmc_ctx *ctx, vmc_lists *L, double eps_run) {
         ds_len[t] = count_above(L->h_ds_key + L->h_ds_off[t], L->h_ds_off[t + 1] - L->h_ds_off[t], eps_run);
     for (int t = 0; t < M * M; ++t)
         do_len[t] = count_above(L->h_do_key + L->h_do_off[t], L->h_do_off[t + 1] - L->h_do_off[t], eps_run);
+    std::vector<uint4> tab;
+    build_unit_table(L, s_len.data(), ds_len.data(), do_len.data(), tab);
     cudaError_t e;
-    e = cudaMemcpyAsync((void *)L->view.s_len, s_len.data(), sizeof(uint32_t) * M, cudaMemcpyHostToDevice, ctx->stream);
+    e = cudaMemcpyAsync((void *)L->view.unit_tab, tab.data(), sizeof(uint4) * tab.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)L->view.s_len, s_len.data(), sizeof(uint32_t) * M, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess && npair > 0)
         e = cudaMemcpyAsync((void *)L->view.ds_len, ds_len.data(), sizeof(uint32_t) * npair, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
@@ -333,6 +395,24 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
         Tjkf[k] = (float)H.Tjk[k];
     }
 
+    // ---- work-unit geometry (see build_unit_table)
+    ListsView &v = L->view;
+    v.M = M; v.ns = ns; v.nds = nds; v.ndo = ndo; v.e_core = e_core; v.ns_pad = ns_pad;
+    {
+        const int band = H.band;
+        // candidates of an alpha row: same-spin q in (p, p+band], opposite q in [p-band, p+band];
+        // no row groups at all when every double list is empty (e.g. the Hubbard model)
+        bool any_double = nds > 0 || ndo > 0;
+        const int cand = std::min(band, M - 1) + std::min(2 * band + 1, M);
+        v.band = band;
+        v.cpr = any_double ? std::max(1, (cand + 31) / 32) : 0;
+        // beta rows have at most `band` candidates: 32 / band of them share one warp group
+        v.rpg = (band >= 1 && band <= 32) ? 32 / band : 1;
+        v.cpr_b = band <= 32 ? 1 : (band + 31) / 32;
+        const int nb_groups = (!any_double || band == 0) ? 0 : (v.rpg > 1 ? (M + v.rpg - 1) / v.rpg : M * v.cpr_b);
+        v.n_groups = (2 * M + 31) / 32 + M * v.cpr + nb_groups;
+    }
+
     // ---- one device allocation
     struct Piece { const void *src; size_t bytes; size_t off; };
     std::vector<Piece> pcs;
@@ -370,6 +450,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     const size_t i_h1 = add(h1, sizeof(double) * MM * MM);
     const size_t i_cf = add(nullptr, sizeof(float) * MM * 2 * MM);
     const size_t i_jsym = add(nullptr, (sizeof(double) + sizeof(float)) * 4 * MM * MM);
+    const size_t i_tab = add(nullptr, sizeof(uint4) * 32 * (size_t)v.n_groups);
 
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce == cudaSuccess) ce = cudaMalloc(&L->dev, off);
@@ -388,22 +469,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
         }
     }
     auto P = [&](size_t idx) { return (void *)(base + pcs[idx].off); };
-    ListsView &v = L->view;
-    v.M = M; v.ns = ns; v.nds = nds; v.ndo = ndo; v.e_core = e_core; v.ns_pad = ns_pad;
-    {
-        const int band = H.band;
-        // candidates of an alpha row: same-spin q in (p, p+band], opposite q in [p-band, p+band];
-        // no row groups at all when every double list is empty (e.g. the Hubbard model)
-        bool any_double = nds > 0 || ndo > 0;
-        const int cand = std::min(band, M - 1) + std::min(2 * band + 1, M);
-        v.band = band;
-        v.cpr = any_double ? std::max(1, (cand + 31) / 32) : 0;
-        // beta rows have at most `band` candidates: 32 / band of them share one warp group
-        v.rpg = (band >= 1 && band <= 32) ? 32 / band : 1;
-        v.cpr_b = band <= 32 ? 1 : (band + 31) / 32;
-        const int nb_groups = (!any_double || band == 0) ? 0 : (v.rpg > 1 ? (M + v.rpg - 1) / v.rpg : M * v.cpr_b);
-        v.n_groups = (2 * M + 31) / 32 + M * v.cpr + nb_groups;
-    }
+    v.unit_tab = (const uint4 *)P(i_tab);
     v.s_off = (const uint32_t *)P(i_s_off); v.s_len = (const uint32_t *)P(i_s_len);
     v.s_owner = (const uint32_t *)P(i_s_owner); v.s_a = (const uint16_t *)P(i_s_a);
     v.s_rec32 = (const float4 *)P(i_s_r32); v.s_rec64 = (const double4_32a *)P(i_s_r64);

@@ -53,6 +53,7 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     m = torch.zeros_like(g)
     v = torch.zeros_like(g)
     AOv, AEOv = eng.split(AO), eng.split(AEO)
+    AOc, AEOc = eng.split_cps(AO), eng.split_cps(AEO)   # correlator coefficients (None without them)
     ne = n_elec or (eng.na + eng.nb)
     rank = 0
     if torch.distributed.is_available() and torch.distributed.is_initialized():
@@ -69,6 +70,8 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
             vmc.vmc_local_energy(eng.ctx, eng.lists, prm, ws, eng.eps, eng.e_loc, eng.t_res)
             if s >= burn_in:
                 vmc.vmc_accumulate_gradient(eng.ctx, ws, eng.t_res, eng.e_loc, AOv, AEOv, sums)
+                if AOc is not None:
+                    vmc.vmc_accumulate_gradient_cps(eng.ctx, ws, prm, eng.t_res, eng.e_loc, AOc, AEOc)
             vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm, ws, D.rank_seed(seed + k, rank), eng.moves)
         D.allreduce_sums(red)
         alpha = alpha_schedule(k, alpha0, alpha1, warm)

@@ -103,22 +103,30 @@ def eps_protocol(name: str = "H20", eps_opt: float = 1e-4, eps_eval=(1e-4, 1e-5,
 def chain_optimisation(names=("H20", "H40", "H80", "H160"), walkers: int = 4096, sweeps: int = 64,
                        burn_in: int = 4, iters: int = 40, eps: float = 1e-6, seed: int = S.MASTER_SEED,
                        alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5,
-                       form: int = vmc.VMC_MIXED) -> dict:
-    """The same optimisation (samples per iteration, schedule) for every chain length."""
+                       form: int = vmc.VMC_MIXED, cps: bool = False, start: str = "core") -> dict:
+    """The same optimisation (samples per iteration, schedule) for every chain length.  cps: the
+    wavefunction is 5-site correlators x Slater determinants (the pair Jastrow set to zero), as in
+    the paper's chain runs; start: the starting determinant (systems.make_params)."""
     out = {"study": "chain_optimisation", "walkers": walkers, "sweeps_per_iteration": sweeps, "burn_in": burn_in,
            "samples_per_iteration": walkers * (sweeps - burn_in), "eps": eps,
            "alpha": {"first": alpha0, "then": alpha1, "after_iterations": warm},
-           "form": "mixed" if form == vmc.VMC_MIXED else "fp64", "systems": {}}
+           "form": "mixed" if form == vmc.VMC_MIXED else "fp64",
+           "wavefunction": ("5-site correlators x Slater" if cps else "pair Jastrow x Slater") + f", {start} start",
+           "systems": {}}
     for name in names:
         sys_ = S.named_system(name)
-        prm = S.make_params(sys_, seed=seed)
+        prm = S.make_params(sys_, seed=seed, start=start, c_noise=0.01 if start == "core" else 0.05)
+        corr = None
+        if cps:
+            prm.J[:] = 0.0
+            corr = S.make_cps(sys_, seed=seed + 7, noise=0.0)
         occ = S.init_occupations(sys_, prm, walkers, seed=seed + 1)
-        eng = vmc.Engine(sys_, prm, occ, eps=eps, precision=form)
+        eng = vmc.Engine(sys_, prm, occ, eps=eps, precision=form, cps=corr)
         vmc.Batch([eng]).autotune()
         t0 = time.perf_counter()
         its = O.optimize(eng, iters, sweeps, seed=seed, burn_in=burn_in, n_elec=sys_.n_elec, alpha0=alpha0,
                          alpha1=alpha1, warm=warm)
-        out["systems"][name] = {"energy_per_electron": [it.energy_per_electron for it in its],
+        out["systems"][name] = {"n_params": eng.n_params, "energy_per_electron": [it.energy_per_electron for it in its],
                                 "t_sum": [it.t_sum for it in its], "ms_per_iteration": float(np.median([it.ms for it in its])),
                                 "wall_s": time.perf_counter() - t0}
         eng.close()
@@ -136,13 +144,17 @@ def main():
     ap.add_argument("--sweeps", type=int, default=64)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--out", default="")
+    ap.add_argument("--eps", type=float, default=0.0, help="chains: screening threshold (0: 1e-6)")
+    ap.add_argument("--cps", action="store_true", help="chains: 5-site correlators x Slater")
+    ap.add_argument("--start", default="core", choices=["core", "neel"])
     args = ap.parse_args()
     if args.study == "eps":
         res = [eps_protocol(n, walkers=args.walkers or 2048, sweeps=args.sweeps, iters=args.iters)
                for n in (args.systems or "H20,H40").split(",")]
     else:
         res = chain_optimisation(tuple((args.systems or "H20,H40,H80,H160").split(",")), walkers=args.walkers or 4096,
-                                 sweeps=args.sweeps, iters=args.iters)
+                                 sweeps=args.sweeps, iters=args.iters, eps=args.eps or 1e-6, cps=args.cps,
+                                 start=args.start)
     text = json.dumps(res)
     print(text, flush=True)
     if args.out:

@@ -316,13 +316,26 @@ def core_orbitals(h1: np.ndarray, n: int) -> np.ndarray:
     return V
 
 
+def neel_orbitals(M: int, n: int, offset: int) -> np.ndarray:
+    """Local orbitals on alternating sites offset, offset + 2, ... (n columns of the identity): the
+    antiferromagnetic determinant of a stretched chain in local orbitals, alpha on even sites and
+    beta on odd ones, the shape a broken-symmetry (unrestricted) mean-field solution takes there."""
+    sites = [(offset + 2 * k) % M for k in range(n)]
+    if len(set(sites)) != n:
+        raise ValueError("more electrons of one spin than alternating sites")
+    C = np.zeros((M, n))
+    C[sites, np.arange(n)] = 1.0
+    return C
+
+
 def make_params(sys: System, seed: int = MASTER_SEED, j_scale: float = 0.01,
                 c_noise: float = 0.01, zero_jastrow: bool = False,
-                exact_planewave: bool = False) -> Params:
+                exact_planewave: bool = False, start: str = "core") -> Params:
     """Seeded Jastrow-Slater parameters.
 
     Slater part: Hubbard rings use real plane waves, everything else the core-Hamiltonian
-    orbitals; both get an independent N(0, c_noise) perturbation per spin (unrestricted).
+    orbitals (start="core") or the alternating-site determinant (start="neel"); both get an
+    independent N(0, c_noise) perturbation per spin (unrestricted).
     Jastrow: J ~ N(0, j_scale), symmetric, over spin-orbital pairs.
     """
     rng = np.random.default_rng(seed)
@@ -331,6 +344,9 @@ def make_params(sys: System, seed: int = MASTER_SEED, j_scale: float = 0.01,
     if sys.name.startswith("hubbard") and sys.meta.get("Ly", 1) == 1:
         Ca = planewave_ring(M, sys.n_alpha)
         Cb = planewave_ring(M, sys.n_beta)
+    elif start == "neel":
+        Ca = neel_orbitals(M, sys.n_alpha, 0)
+        Cb = neel_orbitals(M, sys.n_beta, 1)
     else:
         Ca = core_orbitals(sys.h1, sys.n_alpha)
         Cb = core_orbitals(sys.h1, sys.n_beta)
