@@ -27,6 +27,10 @@ class Iteration:
     t_sum: float
     grad_norm: float
     ms: float                  # device time of the iteration (CUDA events)
+    rate_overflow: bool = False   # a CTMC rate reached the fixed-point limit in this iteration
+
+
+RATE_OVERFLOW = 6      # VMC_ERR_OVERFLOW
 
 
 def alpha_schedule(k: int, alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5) -> float:
@@ -42,6 +46,12 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     Each iteration: `sweeps` CTMC steps; the first `burn_in` of them move the walkers without
     entering the sums.  Under an initialised process group the walker sums of all ranks are added
     before the gradient is formed, so every rank applies the same update.
+
+    A CTMC rate at or above the fixed-point limit 2^43 (a walker on a near-node determinant of the
+    current wavefunction, whose neighbour has a ratio that large) is clamped by the library and
+    reported through the latched VMC_ERR_OVERFLOW; such a walker's residence time is below 2^-43,
+    so its weight in the sums is nil.  The loop records the event in the iteration and continues;
+    every other latched error is raised.
     """
     if sweeps <= burn_in:
         raise ValueError("sweeps must exceed burn_in")
@@ -79,9 +89,11 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
         vmc.vmc_amsgrad_update(eng.ctx, eng.p, g, m, v, alpha, beta1, beta2)
         vmc.vmc_walkers_refresh(eng.ctx, eng.lists, prm, ws)
         b.record(stream)
-        eng.sync()
+        st = vmc.lib().vmc_sync(eng.ctx)             # waits for the stream, returns and clears the flags
+        if st not in (0, RATE_OVERFLOW):
+            vmc._check(eng.ctx, st)
         T, TE = (float(x) for x in sums.cpu())
-        it = Iteration(k, alpha, TE / T, TE / T / ne, T, float(g.norm()), a.elapsed_time(b))
+        it = Iteration(k, alpha, TE / T, TE / T / ne, T, float(g.norm()), a.elapsed_time(b), st == RATE_OVERFLOW)
         out.append(it)
         if callback is not None:
             callback(it)

@@ -128,6 +128,7 @@ def chain_optimisation(names=("H20", "H40", "H80", "H160"), walkers: int = 4096,
                          alpha1=alpha1, warm=warm)
         out["systems"][name] = {"n_params": eng.n_params, "energy_per_electron": [it.energy_per_electron for it in its],
                                 "t_sum": [it.t_sum for it in its], "ms_per_iteration": float(np.median([it.ms for it in its])),
+                                "rate_overflow_iterations": [it.index for it in its if it.rate_overflow],
                                 "wall_s": time.perf_counter() - t0}
         eng.close()
         del eng
@@ -147,6 +148,7 @@ def main():
     ap.add_argument("--eps", type=float, default=0.0, help="chains: screening threshold (0: 1e-6)")
     ap.add_argument("--cps", action="store_true", help="chains: 5-site correlators x Slater")
     ap.add_argument("--start", default="core", choices=["core", "neel"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.study == "eps":
         res = [eps_protocol(n, walkers=args.walkers or 2048, sweeps=args.sweeps, iters=args.iters)
@@ -154,7 +156,7 @@ def main():
     else:
         res = chain_optimisation(tuple((args.systems or "H20,H40,H80,H160").split(",")), walkers=args.walkers or 4096,
                                  sweeps=args.sweeps, iters=args.iters, eps=args.eps or 1e-6, cps=args.cps,
-                                 start=args.start)
+                                 start=args.start, form=vmc.VMC_FP64 if args.form == "fp64" else vmc.VMC_MIXED)
     text = json.dumps(res)
     print(text, flush=True)
     if args.out:
