@@ -40,7 +40,8 @@ def alpha_schedule(k: int, alpha0: float = 0.001, alpha1: float = 0.01, warm: in
 
 def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_in: int = 0,
              alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5, beta1: float = 0.1,
-             beta2: float = 0.01, n_elec: int | None = None, callback=None) -> list[Iteration]:
+             beta2: float = 0.01, n_elec: int | None = None, callback=None,
+             train_jastrow: bool = True) -> list[Iteration]:
     """Run n_iter AMSGrad iterations on `eng` (its parameters eng.p are updated in place).
 
     Each iteration: `sweeps` CTMC steps; the first `burn_in` of them move the walkers without
@@ -52,6 +53,10 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     reported through the latched VMC_ERR_OVERFLOW; such a walker's residence time is below 2^-43,
     so its weight in the sums is nil.  The loop records the event in the iteration and continues;
     every other latched error is raised.
+
+    train_jastrow=False keeps the pair-Jastrow block fixed: the energy gradient and the AMSGrad
+    step cover the Slater coefficients and correlator coefficients only (the flat parameters are
+    [J | C_alpha | C_beta | correlators], so this is the tail of the buffers).
     """
     if sweeps <= burn_in:
         raise ValueError("sweeps must exceed burn_in")
@@ -85,8 +90,9 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
             vmc.vmc_ctmc_step(eng.ctx, eng.lists, prm, ws, D.rank_seed(seed + k, rank), eng.moves)
         D.allreduce_sums(red)
         alpha = alpha_schedule(k, alpha0, alpha1, warm)
-        vmc.vmc_energy_gradient(eng.ctx, sums, AO, AEO, g)
-        vmc.vmc_amsgrad_update(eng.ctx, eng.p, g, m, v, alpha, beta1, beta2)
+        j0 = 0 if train_jastrow else (2 * eng.M) ** 2
+        vmc.vmc_energy_gradient(eng.ctx, sums, AO[j0:], AEO[j0:], g[j0:])
+        vmc.vmc_amsgrad_update(eng.ctx, eng.p[j0:], g[j0:], m[j0:], v[j0:], alpha, beta1, beta2)
         vmc.vmc_walkers_refresh(eng.ctx, eng.lists, prm, ws)
         b.record(stream)
         st = vmc.lib().vmc_sync(eng.ctx)             # waits for the stream, returns and clears the flags

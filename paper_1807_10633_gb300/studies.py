@@ -105,8 +105,8 @@ def chain_optimisation(names=("H20", "H40", "H80", "H160"), walkers: int = 4096,
                        alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5,
                        form: int = vmc.VMC_MIXED, cps: bool = False, start: str = "core") -> dict:
     """The same optimisation (samples per iteration, schedule) for every chain length.  cps: the
-    wavefunction is 5-site correlators x Slater determinants (the pair Jastrow set to zero), as in
-    the paper's chain runs; start: the starting determinant (systems.make_params)."""
+    wavefunction is 5-site correlators x Slater determinants (the pair Jastrow set to zero and kept
+    fixed), as in the paper's chain runs; start: the starting determinant (systems.make_params)."""
     out = {"study": "chain_optimisation", "walkers": walkers, "sweeps_per_iteration": sweeps, "burn_in": burn_in,
            "samples_per_iteration": walkers * (sweeps - burn_in), "eps": eps,
            "alpha": {"first": alpha0, "then": alpha1, "after_iterations": warm},
@@ -125,7 +125,7 @@ def chain_optimisation(names=("H20", "H40", "H80", "H160"), walkers: int = 4096,
         vmc.Batch([eng]).autotune()
         t0 = time.perf_counter()
         its = O.optimize(eng, iters, sweeps, seed=seed, burn_in=burn_in, n_elec=sys_.n_elec, alpha0=alpha0,
-                         alpha1=alpha1, warm=warm)
+                         alpha1=alpha1, warm=warm, train_jastrow=not cps)
         out["systems"][name] = {"n_params": eng.n_params, "energy_per_electron": [it.energy_per_electron for it in its],
                                 "t_sum": [it.t_sum for it in its], "ms_per_iteration": float(np.median([it.ms for it in its])),
                                 "rate_overflow_iterations": [it.index for it in its if it.rate_overflow],
