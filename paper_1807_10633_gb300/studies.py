@@ -65,22 +65,34 @@ def sample_energy(eng: vmc.Engine, eps_run: float, sweeps: int, burn_in: int, se
 
 def eps_protocol(name: str = "H20", eps_opt: float = 1e-4, eps_eval=(1e-4, 1e-5, 1e-6, 0.0), walkers: int = 2048,
                  sweeps: int = 64, burn_in: int = 4, iters: int = 40, eval_sweeps: int = 256,
-                 seed: int = S.MASTER_SEED, form: int = vmc.VMC_MIXED) -> dict:
-    """Optimise at eps_opt, then evaluate the optimised wavefunction at every eps in eps_eval."""
+                 seed: int = S.MASTER_SEED, form: int = vmc.VMC_MIXED, cps: bool = False,
+                 start: str = "core") -> dict:
+    """Optimise at eps_opt, then evaluate the optimised wavefunction at every eps in eps_eval.
+    cps: 5-site correlators x Slater with the pair Jastrow zero and fixed (the paper's form)."""
     sys_ = S.named_system(name)
-    prm = S.make_params(sys_, seed=seed)
+    prm = S.make_params(sys_, seed=seed, start=start, c_noise=0.01 if start == "core" else 0.05)
+    corr = None
+    if cps:
+        prm.J[:] = 0.0
+        corr = S.make_cps(sys_, seed=seed + 7, noise=0.0)
     occ = S.init_occupations(sys_, prm, walkers, seed=seed + 1)
-    eng = vmc.Engine(sys_, prm, occ, eps=eps_opt, precision=form)
+    eng = vmc.Engine(sys_, prm, occ, eps=eps_opt, precision=form, cps=corr)
     vmc.Batch([eng]).autotune()
-    its = O.optimize(eng, iters, sweeps, seed=seed, burn_in=burn_in, n_elec=sys_.n_elec)
-    p_opt = eng.p.detach().cpu().numpy()
+    its = O.optimize(eng, iters, sweeps, seed=seed, burn_in=burn_in, n_elec=sys_.n_elec, train_jastrow=not cps)
+    J, Ca, Cb = (x.detach().cpu().numpy().copy() for x in (eng.J, eng.Ca, eng.Cb))
+    opt = S.Params(J, Ca, Cb)
+    corr_opt = None
+    if cps:
+        c = eng.c.detach().cpu().numpy()
+        vals, o = [], 0
+        for st in corr.sites:
+            vals.append(c[o:o + 4 ** len(st)].copy())
+            o += 4 ** len(st)
+        corr_opt = S.CPS(corr.sites, vals)
     eng.close()
-    N2, M = 2 * sys_.M, sys_.M
-    opt = S.Params(p_opt[:N2 * N2].reshape(N2, N2), p_opt[N2 * N2:N2 * N2 + M * sys_.n_alpha].reshape(M, sys_.n_alpha),
-                   p_opt[N2 * N2 + M * sys_.n_alpha:].reshape(M, sys_.n_beta))
     rows = []
     for eps in eps_eval:
-        ev = vmc.Engine(sys_, opt, occ, eps=eps, precision=form)
+        ev = vmc.Engine(sys_, opt, occ, eps=eps, precision=form, cps=corr_opt)
         vmc.Batch([ev]).autotune()
         e, err, ms = sample_energy(ev, eps, eval_sweeps, 16, seed + 99)
         ns, nd, no = vmc.vmc_lists_info(ev.lists)
@@ -94,6 +106,7 @@ def eps_protocol(name: str = "H20", eps_opt: float = 1e-4, eps_eval=(1e-4, 1e-5,
         r["minus_tightest_mEh_per_electron"] = 1e3 * (r["energy_per_electron"] - ref["energy_per_electron"])
         r["difference_error_mEh_per_electron"] = 1e3 * math.hypot(r["error"], ref["error"])
     return {"study": "eps_protocol", "system": name, "eps_opt": eps_opt, "walkers": walkers,
+            "wavefunction": ("5-site correlators x Slater" if cps else "pair Jastrow x Slater") + f", {start} start",
             "sweeps_per_iteration": sweeps, "burn_in": burn_in, "iterations": iters,
             "form": "mixed" if form == vmc.VMC_MIXED else "fp64",
             "optimisation_last_energy_per_electron": its[-1].energy_per_electron,
@@ -151,7 +164,8 @@ def main():
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.study == "eps":
-        res = [eps_protocol(n, walkers=args.walkers or 2048, sweeps=args.sweeps, iters=args.iters)
+        res = [eps_protocol(n, walkers=args.walkers or 2048, sweeps=args.sweeps, iters=args.iters, cps=args.cps,
+                            start=args.start, form=vmc.VMC_FP64 if args.form == "fp64" else vmc.VMC_MIXED)
                for n in (args.systems or "H20,H40").split(",")]
     else:
         res = chain_optimisation(tuple((args.systems or "H20,H40,H80,H160").split(",")), walkers=args.walkers or 4096,
