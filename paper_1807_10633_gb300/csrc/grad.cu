@@ -6,6 +6,8 @@
 // second kernel adds in chunk order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -33,14 +35,19 @@ __device__ __forceinline__ void weights(int mode, const double *t, const double 
 
 // Fixed-point weights for the Jastrow gradient: cq = round(c 2^s) with s chosen from sum |c| so that
 // no partial sum can overflow 63 bits; integer sums are then exact and order independent.
-// Also adds sum c0 and sum c1 to sums[0..1] (mode 1).  One CTA.
-__global__ void __launch_bounds__(1024)
-k_weight_prep(int W, const double *__restrict__ t, const double *__restrict__ e, int mode,
-              long long *__restrict__ cq, int *__restrict__ sexp, double *__restrict__ sums) {
-    __shared__ double r[4][32];
-    __shared__ int s_exp[2];
+// Also adds sum c0 and sum c1 to sums[0..1] (mode 1).  Three launches, each sum in a fixed order:
+// per-CTA partial sums over consecutive walker chunks, one warp that adds the partials and sets the
+// exponents, then the quantisation over the whole grid.
+constexpr int kWeightChunk = 256;   // walkers per partial-sum CTA
+constexpr int kWeightParts = 256;   // most partial sums (chunks grow beyond 65,536 walkers)
+
+__global__ void __launch_bounds__(256)
+k_weight_partial(int W, int chunk, const double *__restrict__ t, const double *__restrict__ e, int mode,
+                 double *__restrict__ part) {
+    __shared__ double r[4][8];
     double a0 = 0.0, a1 = 0.0, s0 = 0.0, s1 = 0.0;
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const int w0 = blockIdx.x * chunk, w1 = min(W, w0 + chunk);
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         double c0, c1;
         weights(mode, t, e, w, c0, c1);
         a0 += fabs(c0); a1 += fabs(c1); s0 += c0; s1 += c1;
@@ -49,21 +56,37 @@ k_weight_prep(int W, const double *__restrict__ t, const double *__restrict__ e,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) { r[0][warp] = a0; r[1][warp] = a1; r[2][warp] = s0; r[3][warp] = s1; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double A0 = 0.0, A1 = 0.0, S0 = 0.0, S1 = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { A0 += r[0][k]; A1 += r[1][k]; S0 += r[2][k]; S1 += r[3][k]; }
-        s_exp[0] = A0 > 0.0 ? 61 - ilogb(A0) : 0;
-        s_exp[1] = A1 > 0.0 ? 61 - ilogb(A1) : 0;
-        sexp[0] = s_exp[0];
-        sexp[1] = s_exp[1];
-        if (sums) { sums[0] += S0; sums[1] += S1; }
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += r[threadIdx.x][k];
+        part[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
     }
-    __syncthreads();
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+}
+
+__global__ void __launch_bounds__(32)
+k_weight_finish(int n_parts, const double *__restrict__ part, int *__restrict__ sexp, double *__restrict__ sums) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < n_parts; b += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] += part[(size_t)b * 4 + q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = warp_sum_f64(v[q]);
+    if (threadIdx.x == 0) {
+        sexp[0] = v[0] > 0.0 ? 61 - ilogb(v[0]) : 0;
+        sexp[1] = v[1] > 0.0 ? 61 - ilogb(v[1]) : 0;
+        if (sums) { sums[0] += v[2]; sums[1] += v[3]; }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_weight_quant(int W, const double *__restrict__ t, const double *__restrict__ e, int mode,
+               const int *__restrict__ sexp, long long *__restrict__ cq) {
+    const int e0 = sexp[0], e1 = sexp[1];
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
         double c0, c1;
         weights(mode, t, e, w, c0, c1);
-        cq[w] = __double2ll_rn(scalbn(c0, s_exp[0]));
-        if (mode) cq[W + w] = __double2ll_rn(scalbn(c1, s_exp[1]));
+        cq[w] = __double2ll_rn(scalbn(c0, e0));
+        if (mode) cq[W + w] = __double2ll_rn(scalbn(c1, e1));
     }
 }
 
@@ -326,16 +349,25 @@ static vmc_status grad_impl(vmc_ctx *ctx, const vmc_walkers *Wk, const double *t
     }
     const int nmax = na > nb ? na : nb, nout = mode + 1;
     if (nmax > 128) return set_err(ctx, VMC_ERR_ARG, "n_sigma > 128 is not supported by the gradient kernel");
-    const size_t head = 256 + sizeof(long long) * 2 * (size_t)W;
+    // workspace: [exponents | pad to 256] [partial weight sums] [cq: 2 W int64] [gradient partials]
+    const size_t parts = 256 + sizeof(double) * 4 * kWeightParts;
+    const size_t head = parts + sizeof(long long) * 2 * (size_t)W;
     const size_t bytes_J = sizeof(long long) * (size_t)nout * cj * N2 * N2;
     const size_t bytes_C = sizeof(double) * (size_t)nout * cc * 2 * M * nmax;
     vmc_status st = ensure_workspace(ctx, head + (bytes_J > bytes_C ? bytes_J : bytes_C));
     if (st) return st;
     int *sexp = (int *)ctx->ws;
-    long long *cq = (long long *)((char *)ctx->ws + 256);
+    double *wpart = (double *)((char *)ctx->ws + 256);
+    long long *cq = (long long *)((char *)ctx->ws + parts);
     void *part = (char *)ctx->ws + head;
-    k_weight_prep<<<1, 1024, 0, ctx->stream>>>(W, t, e, mode, cq, sexp, sums);
-    ctx->launches += 1;
+    {
+        const int wchunk = std::max(kWeightChunk, (W + kWeightParts - 1) / kWeightParts);
+        const int n_parts = (W + wchunk - 1) / wchunk;
+        k_weight_partial<<<n_parts, 256, 0, ctx->stream>>>(W, wchunk, t, e, mode, wpart);
+        k_weight_finish<<<1, 32, 0, ctx->stream>>>(n_parts, wpart, sexp, sums);
+        k_weight_quant<<<(W + 255) / 256 < 1216 ? (W + 255) / 256 : 1216, 256, 0, ctx->stream>>>(W, t, e, mode, sexp, cq);
+        ctx->launches += 3;
+    }
     if (out0[0]) {
         if (jtc) {
             st = launch_grad_J_umma(ctx, W, M, Wk->occ_bits, cq, mode, (long long *)part, chunk_j, cj);
