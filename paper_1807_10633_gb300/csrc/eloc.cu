@@ -378,86 +378,63 @@ __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real>
     }
 }
 
-// Walk the lists of one group's active units, concatenated in lane order (packed walk): each pass
-// reads 32 consecutive entries of the concatenation, one per lane; lane l finds the unit holding
-// flat entry f = c0 + l by a binary search of the inclusive length prefix (incl) over the lanes,
-// loads the entry's 2- or 4-byte key, tests the target orbital(s) in the shared orbital map and
-// queues the free entries (queue 0: singles or same-spin doubles, queue 1: opposite-spin doubles);
-// every 32 queued entries are evaluated at once.  Entry code = list index << 5 | unit lane.  A unit
-// therefore costs no pass of its own: a group's units share passes, the last one partly filled.
-// pos and the queues are addressed as 32-bit shared-memory addresses.
-template <bool kSingles, typename real, typename acc_t, bool kC>
-__device__ __forceinline__ void walk_group(const ListsView &L, const View<real> &V, uint32_t total, uint32_t incl,
-                                           uint32_t cstart, uint32_t cbase, uint32_t csent, int cmeta, uint32_t *wq,
-                                           int lane, unsigned lt_mask, int cci, int ccj, real ceinv, int cii, int cjj,
-                                           acc_t &e_grp, u128 &q_grp, unsigned &flag) {
+// Packed walk over a range [f0, f1) of the concatenated lists of a group's active units, all of
+// entry kind K (compile time).  The active units sit in lanes 0 .. n_act-1 in canonical order, with
+// strictly increasing inclusive length prefix incl.  Each pass reads 32 consecutive entries of the
+// concatenation, one per lane: lane l takes flat entry f = c0 + l, whose unit is the number of units
+// ending at or before f, counted as the units ending at or before c0 (a ballot) plus those ending
+// inside the pass (one bit each, gathered by a warp OR-reduction, then a popcount below the lane).
+// Each lane loads its entry's 2- or 4-byte key, tests the target orbital(s) in the shared orbital
+// map and queues the free entries; every 32 queued entries are evaluated at once.  Entry code =
+// list index << 5 | unit lane.  Lanes past f1 test the key naming their unit's own (occupied)
+// orbitals, so the test needs no bounds branch.  pos and the queues are 32-bit shared addresses.
+template <int K, typename real, typename acc_t, bool kC>
+__device__ __forceinline__ void walk_range(const ListsView &L, const View<real> &V, uint32_t f0, uint32_t f1,
+                                           int n_act, uint32_t incl, uint32_t cstart, uint32_t cbase, uint32_t csent,
+                                           int cmeta, int cls_row, uint32_t *wq, int &qn, int lane, unsigned lt_mask,
+                                           int cci, int ccj, real ceinv, int cii, int cjj, acc_t &e_grp, u128 &q_grp,
+                                           unsigned &flag) {
     const int M = V.geo.M;
     const uint32_t sPos = (uint32_t)__cvta_generic_to_shared(V.pos);
-    const uint32_t sQ0 = (uint32_t)__cvta_generic_to_shared(wq), sQ1 = sQ0 + 256u;
-    int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
-    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+    uint32_t *q = K == 2 ? wq + 64 : wq;
+    const uint32_t sQ = (uint32_t)__cvta_generic_to_shared(q);
+    const bool mine = lane < n_act;
+    const uint32_t low = lane == 31 ? 0xFFFFFFFEu : ((2u << lane) - 2u);   // bits 1 .. lane
+    const uint32_t oA = K == 2 ? 0u : (uint32_t)(cls_row * M), oB = K == 2 ? (uint32_t)M : oA;
+    for (uint32_t c0 = f0; c0 < f1; c0 += 32) {
         const uint32_t f = c0 + lane;
-        int su = 0;
-#pragma unroll
-        for (int st = 16; st >= 1; st >>= 1)
-            if (__shfl_sync(0xffffffffu, incl, su + st - 1) <= f) su += st;
+        const unsigned before = __ballot_sync(0xffffffffu, mine && incl <= c0);
+        const uint32_t end = incl - c0;
+        const uint32_t inside = __reduce_or_sync(0xffffffffu, (mine && incl > c0 && end < 32u) ? (1u << end) : 0u);
+        const int su = min(31, __popc(before) + __popc(inside & low));
         const uint32_t ub = __shfl_sync(0xffffffffu, cbase, su), us = __shfl_sync(0xffffffffu, cstart, su);
         const uint32_t usent = __shfl_sync(0xffffffffu, csent, su);
-        const bool valid = f < total;
+        const bool valid = f < f1;
         const uint32_t idx = ub + (f - us);
         uint32_t x, y = 0xFFFFu;
-        bool p0, p1;
-        if (kSingles) {
+        if (K == 0) {
             const int cls = __shfl_sync(0xffffffffu, cmeta, su) >> 2;
             const uint32_t key = valid ? (uint32_t)__ldg(&L.s_a[idx]) : usent;
             asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * ((uint32_t)(cls * M) + (key & 0xFFFFu))));
-            p0 = valid && (x & 0x8000u);
-            p1 = false;
         } else {
-            const int um = __shfl_sync(0xffffffffu, cmeta, su), kind = um & 3, cls = um >> 2;
-            const uint32_t key = valid ? __ldg((kind == 2 ? L.do_ab : L.ds_ab) + idx) : usent;
-            const uint32_t oA = kind == 2 ? 0u : (uint32_t)(cls * M), oB = kind == 2 ? (uint32_t)M : oA;
+            const uint32_t key = valid ? __ldg((K == 2 ? L.do_ab : L.ds_ab) + idx) : usent;
             asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * (oA + (key & 0xFFFFu))));
             asm("ld.shared.u16 %0, [%1];" : "=r"(y) : "r"(sPos + 2u * (oB + (key >> 16))));
-            const bool pass = valid && (x & y & 0x8000u);
-            p0 = pass && kind != 2;
-            p1 = pass && kind == 2;
         }
-        const unsigned b0 = __ballot_sync(0xffffffffu, p0);
-        const uint32_t code = (idx << 5) | (uint32_t)su;
-        if (p0)
-            asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ0 + 4u * (uint32_t)(qn0 + __popc(b0 & lt_mask))), "r"(code)
-                         : "memory");
-        qn0 += __popc(b0);
-        if (!kSingles) {
-            const unsigned b1 = __ballot_sync(0xffffffffu, p1);
-            if (p1)
-                asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ1 + 4u * (uint32_t)(qn1 + __popc(b1 & lt_mask))),
-                             "r"(code) : "memory");
-            qn1 += __popc(b1);
-        }
-        if (qn0 >= 32) {
+        const bool pass = valid && (x & y & 0x8000u);
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (pass)
+            asm volatile("st.shared.u32 [%0], %1;" ::"r"(sQ + 4u * (uint32_t)(qn + __popc(bal & lt_mask))),
+                         "r"((idx << 5) | (uint32_t)su) : "memory");
+        qn += __popc(bal);
+        if (qn >= 32) {
             __syncwarp();
-            qn0 -= 32;
-            drain_queue<kSingles ? 0 : 1, real, acc_t, kC>(L, V, wq + qn0, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj,
-                                                            e_grp, q_grp, flag);
-            __syncwarp();
-        }
-        if (!kSingles && qn1 >= 32) {
-            __syncwarp();
-            qn1 -= 32;
-            drain_queue<2, real, acc_t, kC>(L, V, wq + 64 + qn1, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp,
-                                            q_grp, flag);
+            qn -= 32;
+            drain_queue<K, real, acc_t, kC>(L, V, q + qn, 32, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                            flag);
             __syncwarp();
         }
     }
-    __syncwarp();
-    if (qn0)
-        drain_queue<kSingles ? 0 : 1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp,
-                                                        q_grp, flag);
-    if (!kSingles && qn1)
-        drain_queue<2, real, acc_t, kC>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp, flag);
-    __syncwarp();
 }
 
 // Local energy of walker w by the whole CTA (any number of warps).  smraw: dynamic shared memory.
@@ -537,30 +514,60 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
     for (int g = warp; g < n_groups;) {
         Unit<real> u;
         const bool act = setup_unit<real>(L, V, g, lane, u);
-        const int cmeta = u.kind | (u.cls << 2);
-        const int cci = u.ci, ccj = u.cj, cii = u.i, cjj = u.j;
-        const real ceinv = u.einv;
         acc_t e_grp = 0;
         u128 q_grp = 0;
-        // inclusive prefix of the active units' list lengths over the lanes
-        const uint32_t mylen = act ? u.len : 0u;
-        uint32_t incl = mylen;
+        unsigned amask = __ballot_sync(0xffffffffu, act);
+        if (__ballot_sync(0xffffffffu, act && u.base + u.len > list_size(L, u.kind))) {   // cannot happen: guard
+            flag |= VMC_DEV_INCONSISTENT;
+            amask = 0;
+        }
+        // compact the active units into lanes 0 .. n_act-1, in order (same-spin units precede the
+        // opposite-spin ones of a row); the queue, empty between groups, holds the permutation
+        const int n_act = __popc(amask);
+        const int n1 = __popc(amask & __ballot_sync(0xffffffffu, u.kind != 2));
+        if ((amask >> lane) & 1u) wq[__popc(amask & lt_mask)] = (uint32_t)lane;
+        __syncwarp();
+        const int src = lane < n_act ? (int)wq[lane] : lane;
+        __syncwarp();
+        const uint32_t clen0 = __shfl_sync(0xffffffffu, u.len, src);
+        const uint32_t clen = lane < n_act ? clen0 : 0u;
+        const uint32_t cbase = __shfl_sync(0xffffffffu, u.base, src), csent = __shfl_sync(0xffffffffu, u.sent, src);
+        const int cmeta = __shfl_sync(0xffffffffu, u.kind | (u.cls << 2), src);
+        const int cci = __shfl_sync(0xffffffffu, u.ci, src), ccj = __shfl_sync(0xffffffffu, u.cj, src);
+        const int cii = kC ? __shfl_sync(0xffffffffu, u.i, src) : 0, cjj = kC ? __shfl_sync(0xffffffffu, u.j, src) : 0;
+        const real ceinv = __shfl_sync(0xffffffffu, u.einv, src);
+        // inclusive prefix of the compacted list lengths; t1 = end of the same-spin (or singles) part
+        uint32_t incl = clen;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += o;
         }
-        uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (__ballot_sync(0xffffffffu, act && u.base + u.len > list_size(L, u.kind))) {   // cannot happen: guard
-            flag |= VMC_DEV_INCONSISTENT;
-            total = 0;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t t1v = __shfl_sync(0xffffffffu, incl, n1 > 0 ? n1 - 1 : 0), t1 = n1 > 0 ? t1v : 0u;
+        const int cls_row = __shfl_sync(0xffffffffu, cmeta, 0) >> 2;   // spin of a row group's same-spin units
+        int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
+        if (g < n_sgl_groups) {
+            walk_range<0, real, acc_t, kC>(L, V, 0, total, n_act, incl, incl - clen, cbase, csent, cmeta, 0, wq, qn0,
+                                           lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            __syncwarp();
+            if (qn0)
+                drain_queue<0, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                                flag);
+        } else {
+            walk_range<1, real, acc_t, kC>(L, V, 0, t1, n_act, incl, incl - clen, cbase, csent, cmeta, cls_row, wq,
+                                           qn0, lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            walk_range<2, real, acc_t, kC>(L, V, t1, total, n_act, incl, incl - clen, cbase, csent, cmeta, cls_row,
+                                           wq, qn1, lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            __syncwarp();
+            if (qn0)
+                drain_queue<1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
+                                                flag);
+            if (qn1)
+                drain_queue<2, real, acc_t, kC>(L, V, wq + 64, qn1, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp,
+                                                q_grp, flag);
         }
-        if (g < n_sgl_groups)
-            walk_group<true, real, acc_t, kC>(L, V, total, incl, incl - mylen, u.base, u.sent, cmeta, wq, lane,
-                                              lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
-        else
-            walk_group<false, real, acc_t, kC>(L, V, total, incl, incl - mylen, u.base, u.sent, cmeta, wq, lane,
-                                               lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+        __syncwarp();
         const double eg_sum = warp_sum_acc(e_grp);   // FP32 lanes in the mixed form: one conversion
         q_grp = warp_sum_u128(q_grp);
         if (lane == 0) {
