@@ -136,9 +136,9 @@ class Clocks:
 # warp instructions (smsp__inst_executed.sum), from the capture summarised in
 # profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel source with this digest
 # only; any later change of the kernel's file reports traffic as null until it is captured again.
-ELOC_COUNTERS = {"sha256": "bb0adc26b5d4ccc970bfefaf0f408e1323ec6044c85095cd9f1e533035845fe8",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80387.7, "l2_bytes_per_walker": 882159.5,
-                 "warp_inst_per_walker": 288949.3}
+ELOC_COUNTERS = {"sha256": "9660f4e1d705ad2a6d8b2af5c9c6ad34812e31e5acd9955a68f442474b2d98a6",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80400.9, "l2_bytes_per_walker": 881493.4,
+                 "warp_inst_per_walker": 256122.1}
 
 
 def counters_apply(system: str, eps: float) -> bool:
