@@ -392,8 +392,13 @@ vmc_status vmc_walker_reduce(vmc_ctx *ctx, int W, const double *d_t_res, const d
 vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w, double *d_dJ,
                                    double *d_dC_alpha, double *d_dC_beta, void *cuda_stream);
 
-/* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the mixed-form refresh forms
-   G = C C_occ^-1 with tcgen05 TF32 MMAs and a split-precision correction (0: FP32 CUDA cores).
+/* Context options.  VMC_OPT_G_TENSOR_CORES (default 1): the refresh forms G = C C_occ^-1 on the
+   tcgen05 tensor cores.  Mixed form: TF32 MMAs with a split-precision correction (0: FP32 CUDA
+   cores).  FP64 form (register Gauss-Jordan refresh, n_sigma <= 128): every row of C and of
+   C_occ^-T is scaled by a power of two and split into six BF16 digits of 8 bits, the digit
+   products are summed exactly in FP32 and combined in 64-bit integers; G differs from the exact
+   product by less than about 2^-44 n_sigma of the product of the two rows' power-of-two scales
+   (0: FP64 FMAs on the CUDA cores).
    VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256, 384 or 512).
    VMC_OPT_MIXED_REFRESH_GJ32 (default 0): how VMC_MIXED recomputes C_occ^-1 at every refresh.
    0: LU with partial pivoting in FP64 in shared memory, the inverse from the factors and G in

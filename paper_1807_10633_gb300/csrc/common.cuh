@@ -42,7 +42,7 @@ struct vmc_ctx {
     int *d_queue = nullptr;
     std::string rates_batch;       // walker tables the batched rate store belongs to
     int eloc_threads = 256;        // threads per local-energy CTA (set by the autotuner)
-    int g_tensor_cores = 1;        // mixed refresh: G on tcgen05 (1) or CUDA cores (0)
+    int g_tensor_cores = 1;        // refresh: G on tcgen05 (1) or CUDA cores (0)
     int refresh_smem = 0;          // refresh: register Gauss-Jordan (0) or shared-memory LU/GJ (1)
     int mixed_gj32 = 0;            // mixed refresh: FP64 LU of C_occ (0) or FP32 register Gauss-Jordan (1)
     int grad_j_tc = 1;             // Jastrow walker sums: tcgen05 digit products (1) or integer pipe (0)
@@ -121,6 +121,7 @@ struct vmc_lists {
     size_t dev_bytes = 0;
     ListsView view{};
     void *cf = nullptr;      // FP32 copy of C_alpha | C_beta (M x 2M floats at most)
+    void *cdig = nullptr;    // FP64-form G: BF16 digit table of C and its row exponents
     void *jsym = nullptr;    // symmetric copies of J: FP64 (2M)^2 then FP32 (2M)^2
     const double *jastrow_for = nullptr;   // J pointer the constants were refreshed for
     uint64_t jastrow_epoch = 0;
@@ -242,6 +243,9 @@ vmc_status launch_local_energy_batch(vmc_ctx *ctx, int n, const vmc_batch_item *
 vmc_status launch_ctmc_step_batch(vmc_ctx *ctx, int n, const vmc_batch_item *items, uint64_t seed);
 vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf);
 size_t g_umma_smem(int M, int na, int nb);
+bool g_ozaki_ok(int M, int na, int nb);
+size_t g_ozaki_table_bytes(int M);
+vmc_status launch_g_ozaki(vmc_ctx *ctx, const vmc_walkers *Wk, const double *Ca, const double *Cb, void *table);
 vmc_status launch_grad_J_umma(vmc_ctx *ctx, int W, int M, const uint32_t *bits, const long long *cq, int mode,
                               long long *part, int chunk, int n_chunks);
 void grad_j_umma_chunks(int W, int M, int nsm, int *chunk, int *n_chunks);

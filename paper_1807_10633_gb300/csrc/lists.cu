@@ -449,6 +449,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     const size_t i_hd = add(H.hd.data(), sizeof(double) * MM);
     const size_t i_h1 = add(h1, sizeof(double) * MM * MM);
     const size_t i_cf = add(nullptr, sizeof(float) * MM * 2 * MM);
+    const size_t i_cdig = add(nullptr, g_ozaki_table_bytes((int)MM));
     const size_t i_jsym = add(nullptr, (sizeof(double) + sizeof(float)) * 4 * MM * MM);
     const size_t i_tab = add(nullptr, sizeof(uint4) * 32 * (size_t)v.n_groups);
 
@@ -484,6 +485,7 @@ extern "C" vmc_status vmc_build_screened_lists(vmc_ctx *ctx, int M, const double
     v.Jd = (const double *)P(i_Jd); v.Kd = (const double *)P(i_Kd);
     v.hd = (const double *)P(i_hd); v.h1 = (const double *)P(i_h1);
     L->cf = P(i_cf);
+    L->cdig = P(i_cdig);
     L->jsym = P(i_jsym);
     // the Jastrow constants are written by the first walker (re)initialisation
     vmc_status st = lists_set_eps(ctx, L, eps);

@@ -498,6 +498,278 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP64-form G = C_v C_occ^-1 on the tensor cores from exact digit products (Sec. III.B, Eq. R).
+//
+// Every FP64 operand row is scaled by a power of two 2^E (|x| < 2^E over the row) and rounded to a
+// 47-bit fixed-point integer, which is split into six balanced base-256 digits,
+//     x = 2^(E-7) sum_i d_i 256^-i  (+ at most 2^(E-48)),   d_0 in [-128, 128], d_i in [-128, 128).
+// BF16 holds every digit exactly, a digit product is an exact 15-bit integer, and the FP32
+// accumulation of one diagonal D_s = sum_{i+j=s} sum_x a_i[c][x] b_j[k][x] stays exact while
+// every partial sum is below 2^24 (at most 6 pairs x 128 columns x 2^14 = 1.26e7).  The epilogue
+// forms T = sum_s D_s 256^(5-s) in 64-bit integers (exact) and G = T 2^(E_c + F_k - 54) with one
+// rounding.  Diagonals s >= 6 are dropped: the result differs from the exact product by less than
+// about 2^-44 n of 2^(E_c + F_k), against about 2^-53 n for an FP64 dot product.
+//
+// CTA = persistent over (spin, walker) items.  Per item: the row exponents E_c of C_occ^-T, then
+// per tile of at most 80 virtual orbitals, the columns x in chunks of 32 (two K = 16 MMA steps):
+// the A digits (C_occ^-T rows, sliced here) and B digits (rows of C gathered from a per-refresh
+// digit table) are staged in a double-buffered pair of K-major core-matrix tiles while the one
+// issuing thread runs the previous chunk's 21 digit-pair MMAs per K step into six FP32
+// accumulators of 80 columns in tensor memory (480 of 512 columns).
+constexpr int kOzS = 6;                 // digits per operand, diagonals kept
+constexpr int kOzKC = 32;               // columns x per staged chunk
+constexpr int kOzN = 80;                // virtual orbitals per tile (accumulator columns)
+constexpr uint32_t kOzA = 16u * (kOzKC / 8) * 128;     // one A digit tile: 128 rows x 32 columns
+constexpr uint32_t kOzB = (kOzN / 8) * (kOzKC / 8) * 128;   // one B digit tile: 80 rows x 32 columns
+constexpr uint32_t kOzBuf = kOzS * (kOzA + kOzB);
+
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, N and M.
+__device__ __forceinline__ uint32_t make_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// biased exponent field of x (0 for zero and subnormals)
+__device__ __forceinline__ int oz_expo(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// The six balanced base-256 digits of round(|x| 2^(47 - E)) with the sign of x, most significant
+// first, for |x| < 2^E (E = the row's largest biased exponent - 1022).  Subnormals count as zero.
+__device__ __forceinline__ void oz_slice(double x, int E, int d[kOzS]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    long long q = 0;
+    if (ex != 0) {
+        const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = 1075 + E - 47 - ex;            // >= 6 because ex <= E + 1022
+        if (sh < 64) {
+            const long long r = (long long)((m + (1ull << (sh - 1))) >> sh);
+            q = (b >> 63) ? -r : r;
+        }
+    }
+#pragma unroll
+    for (int i = kOzS - 1; i > 0; --i) {
+        const int lo = ((int)(q & 0xFF) ^ 0x80) - 0x80;   // in [-128, 128)
+        d[i] = lo;
+        q = (q - lo) / 256;                             // exact: q - lo is a multiple of 256
+    }
+    d[0] = (int)q;                                      // |q| <= 128
+}
+
+// bf16 bits of a small integer (exact for |v| <= 256)
+__device__ __forceinline__ uint32_t oz_bf16(int v) {
+    return __float_as_uint((float)v) >> 16;
+}
+
+// Digit table of C (both spins): cdig[spin][digit][k][Kp] BF16 (zero for x >= n_sigma) and the
+// row exponents cexp[spin][k].  One warp per (spin, orbital).
+__global__ void __launch_bounds__(256)
+k_c_digits(int M, int na, int nb, int Kp, const double *__restrict__ Ca, const double *__restrict__ Cb,
+           uint16_t *__restrict__ cdig, int *__restrict__ cexp) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (gw >= 2 * M) return;
+    const int s = gw / M, k = gw - s * M, n = s ? nb : na;
+    if (n == 0) return;
+    const double *row = (s ? Cb : Ca) + (size_t)k * n;
+    int mx = 0;
+    for (int x = lane; x < n; x += 32) mx = max(mx, oz_expo(row[x]));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const int E = mx - 1022;
+    if (lane == 0) cexp[s * M + k] = E;
+    for (int x = lane; x < Kp; x += 32) {
+        int d[kOzS];
+        oz_slice(x < n ? row[x] : 0.0, E, d);
+#pragma unroll
+        for (int i = 0; i < kOzS; ++i)
+            cdig[(((size_t)s * kOzS + i) * M + k) * Kp + x] = (uint16_t)oz_bf16(d[i]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdig, const int *__restrict__ cexp,
+          const uint16_t *__restrict__ virt_all, const double *__restrict__ AinvT, double *__restrict__ G,
+          unsigned *status) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)sm + 1023) & ~(uintptr_t)1023);
+    __shared__ int expA[128], expB[VMC_MAX_M];
+    __shared__ uint16_t vs[VMC_MAX_M];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const size_t gstride = (size_t)(M - na) * na + (size_t)(M - nb) * nb;
+    const size_t astride = (size_t)na * na + (size_t)nb * nb;
+    const size_t vstride = (size_t)2 * M - na - nb;
+    const int total = 2 * W, per = (total + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * per, t1 = min(total, t0 + per);
+    if (t0 >= t1) return;
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    int gq = 0;                                    // chunks issued by this CTA
+    // wait until the MMAs committed to buffer b have finished
+    auto drain = [&](int b) {
+        if (!pending[b]) return;
+        if (!mbar_wait(&mbar[b], phase[b])) abort_flag = 1;   // every waiter that times out writes 1
+        phase[b] ^= 1u;
+        pending[b] = false;
+    };
+    const int nchunks = (Kp + kOzKC - 1) / kOzKC;
+
+    for (int t = t0; t < t1 && !abort_flag; ++t) {
+        const int s = t >= W, w = t - s * W, n = s ? nb : na, nv = M - n;
+        if (n == 0 || nv == 0) continue;
+        const double *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
+        const uint16_t *vl = virt_all + (size_t)w * vstride + (s ? (size_t)(M - na) : 0);
+        double *Gw = G + (size_t)w * gstride + (s ? (size_t)(M - na) * na : 0);
+        // row exponents of C_occ^-T (one warp per row), virtual orbitals and their exponents
+        for (int c = warp; c < n; c += kThreads / 32) {
+            int mx = 0;
+            for (int x = lane; x < n; x += 32) mx = max(mx, oz_expo(__ldg(At + (size_t)c * n + x)));
+            mx = __reduce_max_sync(0xffffffffu, mx);
+            if (lane == 0) expA[c] = mx - 1022;
+        }
+        for (int v = tid; v < nv; v += kThreads) {
+            const int k = vl[v];
+            vs[v] = (uint16_t)k;
+            expB[v] = cexp[s * M + k];
+        }
+        __syncthreads();
+        for (int v0 = 0; v0 < nv && !abort_flag; v0 += kOzN) {
+            const int nt = min(kOzN, nv - v0), NP = (nt + 15) & ~15;
+            for (int q = 0; q < nchunks; ++q, ++gq) {
+                const int b = gq & 1;
+                drain(b);                              // the MMAs that read this buffer are done
+                __syncthreads();                       // abort_flag is uniform after the barrier
+                if (abort_flag) break;
+                unsigned char *Ab = base + (size_t)b * kOzBuf, *Bb = Ab + kOzS * kOzA;
+                const int x0 = q * kOzKC;
+                // A digits: rows c < n, 8 columns per work item (16 bytes per digit tile)
+                for (int e = tid; e < ((n + 7) >> 3) * (kOzKC / 8) * 8; e += kThreads) {
+                    const int r8 = e & 7, cm = e >> 3, kc = cm % (kOzKC / 8), rg = cm / (kOzKC / 8);
+                    const int c = rg * 8 + r8;
+                    if (c >= n) continue;
+                    const int E = expA[c];
+                    uint32_t wd[kOzS][4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int x = x0 + kc * 8 + 2 * h;
+                        const double v0d = x < n ? __ldg(At + (size_t)c * n + x) : 0.0;
+                        const double v1d = x + 1 < n ? __ldg(At + (size_t)c * n + x + 1) : 0.0;
+                        int d0[kOzS], d1[kOzS];
+                        oz_slice(v0d, E, d0);
+                        oz_slice(v1d, E, d1);
+#pragma unroll
+                        for (int i = 0; i < kOzS; ++i) wd[i][h] = oz_bf16(d0[i]) | (oz_bf16(d1[i]) << 16);
+                    }
+#pragma unroll
+                    for (int i = 0; i < kOzS; ++i)
+                        *(uint4 *)(Ab + (size_t)i * kOzA + (size_t)e * 16) = make_uint4(wd[i][0], wd[i][1], wd[i][2], wd[i][3]);
+                }
+                // B digits: rows v < nt gathered from the digit table of C
+                for (int e = tid; e < ((nt + 7) >> 3) * (kOzKC / 8) * 8; e += kThreads) {
+                    const int r8 = e & 7, cm = e >> 3, kc = cm % (kOzKC / 8), rg = cm / (kOzKC / 8);
+                    const int v = rg * 8 + r8;
+                    if (v >= nt) continue;
+                    const int x = x0 + kc * 8;
+                    uint4 val[kOzS];
+#pragma unroll
+                    for (int i = 0; i < kOzS; ++i)
+                        val[i] = x < Kp ? __ldg((const uint4 *)(cdig + (((size_t)s * kOzS + i) * M + vs[v0 + v]) * Kp + x))
+                                        : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int i = 0; i < kOzS; ++i) *(uint4 *)(Bb + (size_t)i * kOzB + (size_t)e * 16) = val[i];
+                }
+                asm volatile("fence.proxy.async.shared::cta;");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (tid == 0) {
+                    const uint32_t idesc = make_idesc_bf16(kM, NP);
+                    const uint32_t lbo = 128, sbo = (kOzKC / 8) * 128;
+                    const int ksteps = min(kOzKC, Kp - x0) / 16;
+                    for (int ks = 0; ks < ksteps; ++ks)
+#pragma unroll
+                        for (int d = 0; d < kOzS; ++d)
+#pragma unroll
+                            for (int i = 0; i <= d; ++i) {
+                                const uint64_t da = make_desc(smem_u32(Ab + (size_t)i * kOzA) + ks * 256, lbo, sbo);
+                                const uint64_t db = make_desc(smem_u32(Bb + (size_t)(d - i) * kOzB) + ks * 256, lbo, sbo);
+                                const uint32_t accf = (q > 0 || ks > 0 || i > 0) ? 1u : 0u;
+                                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                             ::"r"(tmem + (uint32_t)(d * kOzN)), "l"(da), "l"(db), "r"(idesc), "r"(accf));
+                            }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(smem_u32(&mbar[b])));
+                }
+                pending[b] = true;
+            }
+            drain(0);
+            drain(1);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            __syncthreads();
+            if (abort_flag) break;
+            // epilogue: warp w reads lanes 32 (w % 4) (rows c) and half of the NP columns
+            const int c = (warp & 3) * 32 + lane, half = warp >> 2, hw = NP / 2;
+            const int Ec = c < n ? expA[c] : 0;
+            for (int col0 = half * hw; col0 < half * hw + hw; col0 += 8) {
+                uint32_t r[kOzS][8];
+#pragma unroll
+                for (int d = 0; d < kOzS; ++d) {
+                    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(d * kOzN + col0);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3]), "=r"(r[d][4]),
+                                   "=r"(r[d][5]), "=r"(r[d][6]), "=r"(r[d][7])
+                                 : "r"(taddr));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (c < n) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int v = col0 + j;
+                        if (v < nt) {
+                            long long T = (long long)__float2int_rn(__uint_as_float(r[0][j]));
+#pragma unroll
+                            for (int d = 1; d < kOzS; ++d) T = T * 256 + (long long)__float2int_rn(__uint_as_float(r[d][j]));
+                            const int e2 = Ec + expB[v0 + v] - 54;
+                            Gw[(size_t)(v0 + v) * n + c] =
+                                (e2 >= -1022 && e2 <= 1023)
+                                    ? (double)T * __longlong_as_double((long long)(e2 + 1023) << 52)
+                                    : ldexp((double)T, e2);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(status, VMC_DEV_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
 }  // namespace
 
 // Walker chunking of the tensor-core Jastrow sums: about one CTA per SM over all tiles, chunks a
@@ -560,4 +832,39 @@ vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf) {
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_g_umma");
+}
+
+// FP64-form G from exact digit products: digit table of C, then the persistent tcgen05 kernel.
+bool g_ozaki_ok(int M, int na, int nb) {
+    const int nmax = na > nb ? na : nb;
+    return nmax >= 1 && nmax <= 128 && M <= VMC_MAX_M;
+}
+
+// digit table (2 spins x 6 digits x M rows x Kp BF16, Kp <= M rounded up to 16) + row exponents
+size_t g_ozaki_table_bytes(int M) {
+    const size_t Kp = (size_t)((M + 15) & ~15);
+    return 2 * kOzS * (size_t)M * Kp * sizeof(uint16_t) + 2 * (size_t)M * sizeof(int);
+}
+
+vmc_status launch_g_ozaki(vmc_ctx *ctx, const vmc_walkers *Wk, const double *Ca, const double *Cb, void *table) {
+    const int M = Wk->M, na = Wk->n_alpha, nb = Wk->n_beta, nmax = na > nb ? na : nb;
+    if (!g_ozaki_ok(M, na, nb) || !table) return VMC_ERR_ARG;
+    const int Kp = (nmax + 15) & ~15;
+    uint16_t *cdig = (uint16_t *)table;
+    int *cexp = (int *)(cdig + 2 * kOzS * (size_t)M * Kp);
+    k_c_digits<<<(2 * M * 32 + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, Kp, Ca, Cb, cdig, cexp);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    int dev = 0, nsm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = 2 * (size_t)kOzBuf + 1024;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_g_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::min(nsm, 2 * Wk->W);
+    if (e == cudaSuccess && grid > 0)
+        k_g_ozaki<<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Kp, cdig, cexp, Wk->virt_list,
+                                                         (const double *)Wk->AinvT, (double *)Wk->G, ctx->d_status);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_check(ctx, e, "k_g_ozaki");
 }

@@ -933,7 +933,12 @@ vmc_status launch_init_walkers(vmc_ctx *ctx, vmc_lists *L, const vmc_params *P, 
     if (reg) {
         if (nmax > kGJ * 8) return set_err(ctx, VMC_ERR_ARG, "n_sigma too large for the register inverse (max 128)");
         if (Wk->precision == VMC_FP64) {
-            e = launch_gj<double>(ctx, Wk, P->C_alpha, P->C_beta, 1);
+            const bool oz = ctx->g_tensor_cores && g_ozaki_ok(M, na, nb);
+            e = launch_gj<double>(ctx, Wk, P->C_alpha, P->C_beta, oz ? 0 : 1);
+            if (e == cudaSuccess && oz) {
+                vmc_status st2 = launch_g_ozaki(ctx, Wk, P->C_alpha, P->C_beta, L->cdig);
+                if (st2) return st2;
+            }
         } else {
             float *Cf = (float *)L->cf;
             k_convert_c<<<(M * (na + nb) + 255) / 256, 256, 0, ctx->stream>>>(M, na, nb, P->C_alpha, P->C_beta, Cf);

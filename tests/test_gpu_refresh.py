@@ -1,7 +1,9 @@
 """Walker-table refresh (Sec. III.B): the register-resident Gauss-Jordan inverse (FP64 form; FP32
 option of the mixed form) against an FP64 inverse of C_occ computed here, and against the
 shared-memory kernels (the mixed form's default FP64 LU), for every tile size the register kernel is
-built for (n_sigma up to 16, 64, 80, 96 and 128)."""
+built for (n_sigma up to 16, 64, 80, 96 and 128).  The FP64 form's G from exact digit products on
+the tensor cores is checked against G from FP64 FMAs on the CUDA cores, including more than one
+tile of 80 virtual orbitals and n_sigma = 128."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +13,7 @@ from paper_1807_10633_gb300 import systems as S
 pytestmark = pytest.mark.gpu
 
 # (ring sites, n_alpha, n_beta): register tiles R = ceil(n_max / 16) in {1, 3, 5, 6, 7}
-CASES = [(20, 10, 9), (60, 40, 30), (90, 80, 75), (96, 90, 85), (98, 97, 64)]
+CASES = [(20, 10, 9), (60, 40, 30), (90, 80, 75), (96, 90, 85), (98, 97, 64), (120, 30, 25), (136, 128, 120)]
 
 
 @pytest.fixture(scope="module")
@@ -76,5 +78,43 @@ def test_register_refresh(vmc, case, precision):
                 for k in ("occ_bits", "virt_list", "pos", "S"):
                     assert np.array_equal(reg[k], ref[k]), k
                 assert np.abs(ref["G"] - reg["G"]).max() / scale < 2 * tol
+    finally:
+        eng.close()
+
+
+# (system, walkers): virtual orbitals per spin 10, 80 (one full tile), 90/95 (two tiles), 8/16
+G_CASES = [("H20", 64), ("ring160_80_80", 24), ("ring120_30_25", 40), ("ring136_128_120", 16)]
+
+
+def _g_system(name):
+    if name.startswith("ring"):
+        M, na, nb = (int(x) for x in name[4:].split("_"))
+        return S.hubbard(M, n_alpha=na, n_beta=nb)
+    return S.named_system(name)
+
+
+@pytest.mark.parametrize("case", G_CASES, ids=lambda c: c[0])
+def test_fp64_g_digit_products(vmc, case):
+    """G = C_v C_occ^-1 in the FP64 form: six BF16 digits per operand row on tcgen05 against FP64
+    FMAs (G_TENSOR_CORES = 0), within 1e-12 of max |G|; E_L from both within 1e-11 relative."""
+    name, W = case
+    sys_ = _g_system(name)
+    prm = S.make_params(sys_, seed=21)
+    occ = S.init_occupations(sys_, prm, W, seed=22)
+    eng = vmc.Engine(sys_, prm, occ, eps=1e-6, precision=0)
+    try:
+        tc = _tables(eng)
+        e_tc, _ = eng.local_energy()
+        e_tc = e_tc.cpu().numpy().copy()
+        vmc.vmc_set_option(eng.ctx, vmc.VMC_OPT_G_TENSOR_CORES, 0)
+        eng.refresh()
+        cc = _tables(eng)
+        e_cc, _ = eng.local_energy()
+        e_cc = e_cc.cpu().numpy()
+        for k in ("AinvT", "occ_bits", "virt_list", "pos", "S"):
+            assert np.array_equal(tc[k], cc[k]), k
+        scale = max(1.0, np.abs(cc["G"]).max())
+        assert np.abs(tc["G"] - cc["G"]).max() / scale < 1e-12
+        assert np.abs(e_tc - e_cc).max() / max(1.0, np.abs(e_cc).max()) < 1e-11
     finally:
         eng.close()
