@@ -397,7 +397,7 @@ vmc_status vmc_grad_logpsi_noalloc(const vmc_walkers *walkers, const double *d_w
    cores).  FP64 form (register Gauss-Jordan refresh, n_sigma <= 128): every row of C and of
    C_occ^-T is scaled by a power of two and split into six BF16 digits of 8 bits, the digit
    products are summed exactly in FP32 and combined in 64-bit integers; G differs from the exact
-   product by less than about 2^-44 n_sigma of the product of the two rows' power-of-two scales
+   product by less than about 2^-43 n_sigma of the product of the two rows' power-of-two scales
    (0: FP64 FMAs on the CUDA cores).
    VMC_OPT_ELOC_THREADS: threads per local-energy CTA (128, 256, 384 or 512).
    VMC_OPT_MIXED_REFRESH_GJ32 (default 0): how VMC_MIXED recomputes C_occ^-1 at every refresh.

@@ -502,14 +502,16 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
 // FP64-form G = C_v C_occ^-1 on the tensor cores from exact digit products (Sec. III.B, Eq. R).
 //
 // Every FP64 operand row is scaled by a power of two 2^E (|x| < 2^E over the row) and rounded to a
-// 47-bit fixed-point integer, which is split into six balanced base-256 digits,
-//     x = 2^(E-7) sum_i d_i 256^-i  (+ at most 2^(E-48)),   d_0 in [-128, 128], d_i in [-128, 128).
-// BF16 holds every digit exactly, a digit product is an exact 15-bit integer, and the FP32
-// accumulation of one diagonal D_s = sum_{i+j=s} sum_x a_i[c][x] b_j[k][x] stays exact while
-// every partial sum is below 2^24 (at most 6 pairs x 128 columns x 2^14 = 1.26e7).  The epilogue
-// forms T = sum_s D_s 256^(5-s) in 64-bit integers (exact) and G = T 2^(E_c + F_k - 54) with one
-// rounding.  Diagonals s >= 6 are dropped: the result differs from the exact product by less than
-// about 2^-44 n of 2^(E_c + F_k), against about 2^-53 n for an FP64 dot product.
+// 46-bit fixed-point integer q, which is written in six balanced base-256 digits,
+//     x = 2^(E-6) sum_i d_i 256^-i  (+ at most 2^(E-47)),   d_i in [-128, 128):
+// the digits are the bytes of q + 0x808080808080 minus 128 (that offset adds 128 to every digit
+// position; |q| <= 2^46 keeps the sum inside six bytes).  BF16 holds every digit exactly, a digit
+// product is an exact 15-bit integer, and the FP32 accumulation of one diagonal
+// D_s = sum_{i+j=s} sum_x a_i[c][x] b_j[k][x] stays exact while every partial sum is below 2^24
+// (at most 6 pairs x 128 columns x 2^14 = 1.26e7).  The epilogue forms T = sum_s D_s 256^(5-s) in
+// 64-bit integers (exact) and G = T 2^(E_c + F_k - 52) with one rounding.  Diagonals s >= 6 are
+// dropped: the result differs from the exact product by less than about 2^-43 n of
+// 2^(E_c + F_k), against about 2^-53 n for an FP64 dot product.
 //
 // CTA = persistent over (spin, walker) items.  Per item: the row exponents E_c of C_occ^-T, then
 // per tile of at most 80 virtual orbitals, the columns x in chunks of 32 (two K = 16 MMA steps):
@@ -520,6 +522,7 @@ k_grad_J_umma(int W, int M, int chunk, const uint32_t *__restrict__ bits, const 
 constexpr int kOzS = 6;                 // digits per operand, diagonals kept
 constexpr int kOzKC = 32;               // columns x per staged chunk
 constexpr int kOzN = 80;                // virtual orbitals per tile (accumulator columns)
+constexpr int kOzThreads = 512;         // 16 warps: warp w reads tensor-memory lanes 32 (w % 4)
 constexpr uint32_t kOzA = 16u * (kOzKC / 8) * 128;     // one A digit tile: 128 rows x 32 columns
 constexpr uint32_t kOzB = (kOzN / 8) * (kOzKC / 8) * 128;   // one B digit tile: 80 rows x 32 columns
 constexpr uint32_t kOzBuf = kOzS * (kOzA + kOzB);
@@ -534,36 +537,43 @@ __device__ __forceinline__ int oz_expo(double x) {
     return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// The six balanced base-256 digits of round(|x| 2^(47 - E)) with the sign of x, most significant
-// first, for |x| < 2^E (E = the row's largest biased exponent - 1022).  Subnormals count as zero.
-__device__ __forceinline__ void oz_slice(double x, int E, int d[kOzS]) {
+// round(x 2^(46 - E)) + 0x808080808080 for |x| < 2^E (E = the row's largest biased exponent - 1022);
+// its bytes, least significant first, are the digits d_5 .. d_0 plus 128.  Subnormals count as zero.
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int E) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((b >> 52) & 0x7FF);
     long long q = 0;
     if (ex != 0) {
         const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = 1075 + E - 47 - ex;            // >= 6 because ex <= E + 1022
+        const int sh = 1075 + E - 46 - ex;            // >= 7 because ex <= E + 1022
         if (sh < 64) {
             const long long r = (long long)((m + (1ull << (sh - 1))) >> sh);
             q = (b >> 63) ? -r : r;
         }
     }
-#pragma unroll
-    for (int i = kOzS - 1; i > 0; --i) {
-        const int lo = ((int)(q & 0xFF) ^ 0x80) - 0x80;   // in [-128, 128)
-        d[i] = lo;
-        q = (q - lo) / 256;                             // exact: q - lo is a multiple of 256
-    }
-    d[0] = (int)q;                                      // |q| <= 128
+    return (unsigned long long)(q + 0x808080808080ll);
 }
 
-// bf16 bits of a small integer (exact for |v| <= 256)
-__device__ __forceinline__ uint32_t oz_bf16(int v) {
-    return __float_as_uint((float)v) >> 16;
+// FP32 bit pattern of digit byte k of u (0..5) minus 128: the float 2^23 + byte, less 2^23 + 128
+__device__ __forceinline__ uint32_t oz_digit_f32(uint32_t ulo, uint32_t uhi, int k) {
+    const uint32_t t = k < 4 ? __byte_perm(ulo, 0x4B000000u, 0x7440u | (uint32_t)k)
+                             : __byte_perm(uhi, 0x4B000000u, 0x7440u | (uint32_t)(k - 4));
+    return __float_as_uint(__uint_as_float(t) - 8388736.0f);
+}
+
+// Six BF16 digit words for the element pair (x0, x1), most significant digit first: word i holds
+// digit i of x0 in its low half and of x1 in its high half.
+__device__ __forceinline__ void oz_pair(double x0, double x1, int E, uint32_t w[kOzS]) {
+    const unsigned long long u0 = oz_fixed(x0, E), u1 = oz_fixed(x1, E);
+    const uint32_t a_lo = (uint32_t)u0, a_hi = (uint32_t)(u0 >> 32);
+    const uint32_t b_lo = (uint32_t)u1, b_hi = (uint32_t)(u1 >> 32);
+#pragma unroll
+    for (int i = 0; i < kOzS; ++i)
+        w[i] = __byte_perm(oz_digit_f32(a_lo, a_hi, kOzS - 1 - i), oz_digit_f32(b_lo, b_hi, kOzS - 1 - i), 0x7632u);
 }
 
 // Digit table of C (both spins): cdig[spin][digit][k][Kp] BF16 (zero for x >= n_sigma) and the
-// row exponents cexp[spin][k].  One warp per (spin, orbital).
+// row exponents cexp[spin][k].  One warp per (spin, orbital), two columns per lane and step.
 __global__ void __launch_bounds__(256)
 k_c_digits(int M, int na, int nb, int Kp, const double *__restrict__ Ca, const double *__restrict__ Cb,
            uint16_t *__restrict__ cdig, int *__restrict__ cexp) {
@@ -577,16 +587,16 @@ k_c_digits(int M, int na, int nb, int Kp, const double *__restrict__ Ca, const d
     mx = __reduce_max_sync(0xffffffffu, mx);
     const int E = mx - 1022;
     if (lane == 0) cexp[s * M + k] = E;
-    for (int x = lane; x < Kp; x += 32) {
-        int d[kOzS];
-        oz_slice(x < n ? row[x] : 0.0, E, d);
+    for (int x = 2 * lane; x < Kp; x += 64) {
+        uint32_t w[kOzS];
+        oz_pair(x < n ? row[x] : 0.0, x + 1 < n ? row[x + 1] : 0.0, E, w);
 #pragma unroll
         for (int i = 0; i < kOzS; ++i)
-            cdig[(((size_t)s * kOzS + i) * M + k) * Kp + x] = (uint16_t)oz_bf16(d[i]);
+            *(uint32_t *)(cdig + (((size_t)s * kOzS + i) * M + k) * Kp + x) = w[i];
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kOzThreads, 1)
 k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdig, const int *__restrict__ cexp,
           const uint16_t *__restrict__ virt_all, const double *__restrict__ AinvT, double *__restrict__ G,
           unsigned *status) {
@@ -636,14 +646,20 @@ k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdi
         const double *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
         const uint16_t *vl = virt_all + (size_t)w * vstride + (s ? (size_t)(M - na) : 0);
         double *Gw = G + (size_t)w * gstride + (s ? (size_t)(M - na) * na : 0);
-        // row exponents of C_occ^-T (one warp per row), virtual orbitals and their exponents
-        for (int c = warp; c < n; c += kThreads / 32) {
+        // row exponents of C_occ^-T: four threads per row, their loads all in flight; the virtual
+        // orbitals and their row exponents
+        {
+            const int c = tid >> 2, part = tid & 3;
             int mx = 0;
-            for (int x = lane; x < n; x += 32) mx = max(mx, oz_expo(__ldg(At + (size_t)c * n + x)));
-            mx = __reduce_max_sync(0xffffffffu, mx);
-            if (lane == 0) expA[c] = mx - 1022;
+            if (c < n) {
+#pragma unroll 8
+                for (int x = part; x < n; x += 4) mx = max(mx, oz_expo(__ldg(At + (size_t)c * n + x)));
+            }
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            if (c < n && part == 0) expA[c] = mx - 1022;
         }
-        for (int v = tid; v < nv; v += kThreads) {
+        for (int v = tid; v < nv; v += kOzThreads) {
             const int k = vl[v];
             vs[v] = (uint16_t)k;
             expB[v] = cexp[s * M + k];
@@ -651,6 +667,7 @@ k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdi
         __syncthreads();
         for (int v0 = 0; v0 < nv && !abort_flag; v0 += kOzN) {
             const int nt = min(kOzN, nv - v0), NP = (nt + 15) & ~15;
+            const int nA = ((n + 7) >> 3) * (kOzKC / 8) * 8, nB = ((nt + 7) >> 3) * (kOzKC / 8) * 8;
             for (int q = 0; q < nchunks; ++q, ++gq) {
                 const int b = gq & 1;
                 drain(b);                              // the MMAs that read this buffer are done
@@ -658,41 +675,36 @@ k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdi
                 if (abort_flag) break;
                 unsigned char *Ab = base + (size_t)b * kOzBuf, *Bb = Ab + kOzS * kOzA;
                 const int x0 = q * kOzKC;
-                // A digits: rows c < n, 8 columns per work item (16 bytes per digit tile)
-                for (int e = tid; e < ((n + 7) >> 3) * (kOzKC / 8) * 8; e += kThreads) {
-                    const int r8 = e & 7, cm = e >> 3, kc = cm % (kOzKC / 8), rg = cm / (kOzKC / 8);
-                    const int c = rg * 8 + r8;
-                    if (c >= n) continue;
-                    const int E = expA[c];
-                    uint32_t wd[kOzS][4];
+                // work item = 8 columns of one row: A digits (rows c < n, sliced here), then B digits
+                // (rows v < nt, gathered from the digit table of C); 16 bytes per digit tile each
+                for (int e = tid; e < nA + nB; e += kOzThreads) {
+                    const bool isA = e < nA;
+                    const int ee = isA ? e : e - nA;
+                    const int r8 = ee & 7, cm = ee >> 3, kc = cm % (kOzKC / 8), rg = cm / (kOzKC / 8);
+                    const int r = rg * 8 + r8, x = x0 + kc * 8;
+                    if (isA) {
+                        if (r >= n) continue;
+                        const double *src = At + (size_t)r * n;
+                        double v[8];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int x = x0 + kc * 8 + 2 * h;
-                        const double v0d = x < n ? __ldg(At + (size_t)c * n + x) : 0.0;
-                        const double v1d = x + 1 < n ? __ldg(At + (size_t)c * n + x + 1) : 0.0;
-                        int d0[kOzS], d1[kOzS];
-                        oz_slice(v0d, E, d0);
-                        oz_slice(v1d, E, d1);
+                        for (int h = 0; h < 8; ++h) v[h] = x + h < n ? __ldg(src + x + h) : 0.0;
+                        const int E = expA[r];
+                        uint32_t wd[4][kOzS];
 #pragma unroll
-                        for (int i = 0; i < kOzS; ++i) wd[i][h] = oz_bf16(d0[i]) | (oz_bf16(d1[i]) << 16);
+                        for (int h = 0; h < 4; ++h) oz_pair(v[2 * h], v[2 * h + 1], E, wd[h]);
+#pragma unroll
+                        for (int i = 0; i < kOzS; ++i)
+                            *(uint4 *)(Ab + (size_t)i * kOzA + (size_t)ee * 16) = make_uint4(wd[0][i], wd[1][i], wd[2][i], wd[3][i]);
+                    } else {
+                        if (r >= nt) continue;
+                        uint4 val[kOzS];
+#pragma unroll
+                        for (int i = 0; i < kOzS; ++i)
+                            val[i] = x < Kp ? __ldg((const uint4 *)(cdig + (((size_t)s * kOzS + i) * M + vs[v0 + r]) * Kp + x))
+                                            : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                        for (int i = 0; i < kOzS; ++i) *(uint4 *)(Bb + (size_t)i * kOzB + (size_t)ee * 16) = val[i];
                     }
-#pragma unroll
-                    for (int i = 0; i < kOzS; ++i)
-                        *(uint4 *)(Ab + (size_t)i * kOzA + (size_t)e * 16) = make_uint4(wd[i][0], wd[i][1], wd[i][2], wd[i][3]);
-                }
-                // B digits: rows v < nt gathered from the digit table of C
-                for (int e = tid; e < ((nt + 7) >> 3) * (kOzKC / 8) * 8; e += kThreads) {
-                    const int r8 = e & 7, cm = e >> 3, kc = cm % (kOzKC / 8), rg = cm / (kOzKC / 8);
-                    const int v = rg * 8 + r8;
-                    if (v >= nt) continue;
-                    const int x = x0 + kc * 8;
-                    uint4 val[kOzS];
-#pragma unroll
-                    for (int i = 0; i < kOzS; ++i)
-                        val[i] = x < Kp ? __ldg((const uint4 *)(cdig + (((size_t)s * kOzS + i) * M + vs[v0 + v]) * Kp + x))
-                                        : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                    for (int i = 0; i < kOzS; ++i) *(uint4 *)(Bb + (size_t)i * kOzB + (size_t)e * 16) = val[i];
                 }
                 asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
@@ -724,10 +736,12 @@ k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdi
             asm volatile("tcgen05.fence::after_thread_sync;");
             __syncthreads();
             if (abort_flag) break;
-            // epilogue: warp w reads lanes 32 (w % 4) (rows c) and half of the NP columns
-            const int c = (warp & 3) * 32 + lane, half = warp >> 2, hw = NP / 2;
+            // epilogue: warp w reads lanes 32 (w % 4) (rows c) and the column blocks of 8 with
+            // index = w / 4 modulo 4
+            const int c = (warp & 3) * 32 + lane;
             const int Ec = c < n ? expA[c] : 0;
-            for (int col0 = half * hw; col0 < half * hw + hw; col0 += 8) {
+            for (int cb = warp >> 2; cb < NP / 8; cb += kOzThreads / 128) {
+                const int col0 = cb * 8;
                 uint32_t r[kOzS][8];
 #pragma unroll
                 for (int d = 0; d < kOzS; ++d) {
@@ -746,7 +760,7 @@ k_g_ozaki(int W, int M, int na, int nb, int Kp, const uint16_t *__restrict__ cdi
                             long long T = (long long)__float2int_rn(__uint_as_float(r[0][j]));
 #pragma unroll
                             for (int d = 1; d < kOzS; ++d) T = T * 256 + (long long)__float2int_rn(__uint_as_float(r[d][j]));
-                            const int e2 = Ec + expB[v0 + v] - 54;
+                            const int e2 = Ec + expB[v0 + v] - 52;
                             Gw[(size_t)(v0 + v) * n + c] =
                                 (e2 >= -1022 && e2 <= 1023)
                                     ? (double)T * __longlong_as_double((long long)(e2 + 1023) << 52)
@@ -862,7 +876,7 @@ vmc_status launch_g_ozaki(vmc_ctx *ctx, const vmc_walkers *Wk, const double *Ca,
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_g_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = std::min(nsm, 2 * Wk->W);
     if (e == cudaSuccess && grid > 0)
-        k_g_ozaki<<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Kp, cdig, cexp, Wk->virt_list,
+        k_g_ozaki<<<grid, kOzThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Kp, cdig, cexp, Wk->virt_list,
                                                          (const double *)Wk->AinvT, (double *)Wk->G, ctx->d_status);
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
