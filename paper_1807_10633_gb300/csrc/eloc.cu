@@ -380,44 +380,49 @@ __device__ __forceinline__ void drain_queue(const ListsView &L, const View<real>
 
 // Packed walk over a range [f0, f1) of the concatenated lists of a group's active units, all of
 // entry kind K (compile time).  The active units sit in lanes 0 .. n_act-1 in canonical order, with
-// strictly increasing inclusive length prefix incl.  Each pass reads 32 consecutive entries of the
-// concatenation, one per lane: lane l takes flat entry f = c0 + l, whose unit is the number of units
+// strictly increasing inclusive length prefix incl (the lanes after them hold incl = total).  Each
+// pass reads 32 consecutive entries of the concatenation, one per lane: lane l takes flat entry
+// f = c0 + l, whose unit is the number of units
 // ending at or before f, counted as the units ending at or before c0 (a ballot) plus those ending
 // inside the pass (one bit each, gathered by a warp OR-reduction, then a popcount below the lane).
 // Each lane loads its entry's 2- or 4-byte key, tests the target orbital(s) in the shared orbital
 // map and queues the free entries; every 32 queued entries are evaluated at once.  Entry code =
-// list index << 5 | unit lane.  Lanes past f1 test the key naming their unit's own (occupied)
-// orbitals, so the test needs no bounds branch.  pos and the queues are 32-bit shared addresses.
+// list index << 5 | unit lane; a unit's list index of flat entry f is f + (list base - unit start),
+// one shuffle.  Lanes past f1 read entry 0 of the list (always allocated) and queue nothing, so the
+// test needs no bounds branch.  pos and the queues are 32-bit shared addresses.
 template <int K, typename real, typename acc_t, bool kC>
 __device__ __forceinline__ void walk_range(const ListsView &L, const View<real> &V, uint32_t f0, uint32_t f1,
-                                           int n_act, uint32_t incl, uint32_t cstart, uint32_t cbase, uint32_t csent,
-                                           int cmeta, int cls_row, uint32_t *wq, int &qn, int lane, unsigned lt_mask,
+                                           uint32_t incl, uint32_t cdelta, int cmeta, int cls_row,
+                                           uint32_t *wq, int &qn, int lane, unsigned lt_mask,
                                            int cci, int ccj, real ceinv, int cii, int cjj, acc_t &e_grp, u128 &q_grp,
                                            unsigned &flag) {
     const int M = V.geo.M;
     const uint32_t sPos = (uint32_t)__cvta_generic_to_shared(V.pos);
     uint32_t *q = K == 2 ? wq + 64 : wq;
     const uint32_t sQ = (uint32_t)__cvta_generic_to_shared(q);
-    const bool mine = lane < n_act;
     const uint32_t low = lane == 31 ? 0xFFFFFFFEu : ((2u << lane) - 2u);   // bits 1 .. lane
     const uint32_t oA = K == 2 ? 0u : (uint32_t)(cls_row * M), oB = K == 2 ? (uint32_t)M : oA;
     for (uint32_t c0 = f0; c0 < f1; c0 += 32) {
         const uint32_t f = c0 + lane;
-        const unsigned before = __ballot_sync(0xffffffffu, mine && incl <= c0);
+        // lanes past the active units hold incl = total > c0, so they never count as "before";
+        // a unit ending at or before c0 has end = 0 (bit 0, never counted) or end >= 2^31 (no bit)
+        const unsigned before = __ballot_sync(0xffffffffu, incl <= c0);
         const uint32_t end = incl - c0;
-        const uint32_t inside = __reduce_or_sync(0xffffffffu, (mine && incl > c0 && end < 32u) ? (1u << end) : 0u);
-        const int su = min(31, __popc(before) + __popc(inside & low));
-        const uint32_t ub = __shfl_sync(0xffffffffu, cbase, su), us = __shfl_sync(0xffffffffu, cstart, su);
-        const uint32_t usent = __shfl_sync(0xffffffffu, csent, su);
+        uint32_t bit;
+        asm("shl.b32 %0, 1, %1;" : "=r"(bit) : "r"(end));   // PTX clamps shifts >= 32: no bit
+        const uint32_t inside = __reduce_or_sync(0xffffffffu, bit);
+        // for valid lanes su < n_act; past f1 it may be 32, which the shuffles take modulo 32
+        const int su = __popc(before) + __popc(inside & low);
         const bool valid = f < f1;
-        const uint32_t idx = ub + (f - us);
+        const uint32_t idx = __shfl_sync(0xffffffffu, cdelta, su) + f;   // list base - unit start + f
+        const uint32_t ridx = valid ? idx : 0u;
         uint32_t x, y = 0xFFFFu;
         if (K == 0) {
             const int cls = __shfl_sync(0xffffffffu, cmeta, su) >> 2;
-            const uint32_t key = valid ? (uint32_t)__ldg(&L.s_a[idx]) : usent;
+            const uint32_t key = (uint32_t)__ldg(&L.s_a[ridx]);
             asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * ((uint32_t)(cls * M) + (key & 0xFFFFu))));
         } else {
-            const uint32_t key = valid ? __ldg((K == 2 ? L.do_ab : L.ds_ab) + idx) : usent;
+            const uint32_t key = __ldg((K == 2 ? L.do_ab : L.ds_ab) + ridx);
             asm("ld.shared.u16 %0, [%1];" : "=r"(x) : "r"(sPos + 2u * (oA + (key & 0xFFFFu))));
             asm("ld.shared.u16 %0, [%1];" : "=r"(y) : "r"(sPos + 2u * (oB + (key >> 16))));
         }
@@ -531,7 +536,7 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
         __syncwarp();
         const uint32_t clen0 = __shfl_sync(0xffffffffu, u.len, src);
         const uint32_t clen = lane < n_act ? clen0 : 0u;
-        const uint32_t cbase = __shfl_sync(0xffffffffu, u.base, src), csent = __shfl_sync(0xffffffffu, u.sent, src);
+        const uint32_t cbase = __shfl_sync(0xffffffffu, u.base, src);
         const int cmeta = __shfl_sync(0xffffffffu, u.kind | (u.cls << 2), src);
         const int cci = __shfl_sync(0xffffffffu, u.ci, src), ccj = __shfl_sync(0xffffffffu, u.cj, src);
         const int cii = kC ? __shfl_sync(0xffffffffu, u.i, src) : 0, cjj = kC ? __shfl_sync(0xffffffffu, u.j, src) : 0;
@@ -544,21 +549,22 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
             if (lane >= d) incl += o;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t cdelta = cbase - (incl - clen);   // list index of flat entry f: f + cdelta (mod 2^32)
         const uint32_t t1v = __shfl_sync(0xffffffffu, incl, n1 > 0 ? n1 - 1 : 0), t1 = n1 > 0 ? t1v : 0u;
         const int cls_row = __shfl_sync(0xffffffffu, cmeta, 0) >> 2;   // spin of a row group's same-spin units
         int qn0 = 0, qn1 = 0;   // queue fill (warp-uniform)
         if (g < n_sgl_groups) {
-            walk_range<0, real, acc_t, kC>(L, V, 0, total, n_act, incl, incl - clen, cbase, csent, cmeta, 0, wq, qn0,
-                                           lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            walk_range<0, real, acc_t, kC>(L, V, 0, total, incl, cdelta, cmeta, 0, wq, qn0, lane, lt_mask,
+                                           cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
             __syncwarp();
             if (qn0)
                 drain_queue<0, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
                                                 flag);
         } else {
-            walk_range<1, real, acc_t, kC>(L, V, 0, t1, n_act, incl, incl - clen, cbase, csent, cmeta, cls_row, wq,
-                                           qn0, lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
-            walk_range<2, real, acc_t, kC>(L, V, t1, total, n_act, incl, incl - clen, cbase, csent, cmeta, cls_row,
-                                           wq, qn1, lane, lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            walk_range<1, real, acc_t, kC>(L, V, 0, t1, incl, cdelta, cmeta, cls_row, wq, qn0, lane, lt_mask,
+                                           cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
+            walk_range<2, real, acc_t, kC>(L, V, t1, total, incl, cdelta, cmeta, cls_row, wq, qn1, lane,
+                                           lt_mask, cci, ccj, ceinv, cii, cjj, e_grp, q_grp, flag);
             __syncwarp();
             if (qn0)
                 drain_queue<1, real, acc_t, kC>(L, V, wq, qn0, lane, cci, ccj, ceinv, cmeta, cii, cjj, e_grp, q_grp,
