@@ -136,9 +136,9 @@ class Clocks:
 # warp instructions (smsp__inst_executed.sum), from the capture summarised in
 # profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel source with this digest
 # only; any later change of the kernel's file reports traffic as null until it is captured again.
-ELOC_COUNTERS = {"sha256": "9660f4e1d705ad2a6d8b2af5c9c6ad34812e31e5acd9955a68f442474b2d98a6",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80400.9, "l2_bytes_per_walker": 881493.4,
-                 "warp_inst_per_walker": 256122.1}
+ELOC_COUNTERS = {"sha256": "2d8a0830937f13d48b3ca53be04a07e7df3a378dbe6842f34cef5e243eaf0d6c",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80506.7, "l2_bytes_per_walker": 875875.4,
+                 "warp_inst_per_walker": 219949.0}
 
 
 def counters_apply(system: str, eps: float) -> bool:

@@ -526,9 +526,19 @@ __device__ __forceinline__ void eloc_walker(const ListsView &L, const WalkerArgs
             flag |= VMC_DEV_INCONSISTENT;
             amask = 0;
         }
+        const int n_act = __popc(amask);
+        if (n_act == 0) {                // an empty group (its row orbital unoccupied): zero sums
+            if (lane == 0) {
+                rates[(size_t)w * n_groups + g] = 0;
+                eg[g] = 0.0;
+            }
+            int nxt = 0;
+            if (lane == 0) nxt = atomicAdd(&next_group, 1);
+            g = __shfl_sync(0xffffffffu, nxt, 0);
+            continue;
+        }
         // compact the active units into lanes 0 .. n_act-1, in order (same-spin units precede the
         // opposite-spin ones of a row); the queue, empty between groups, holds the permutation
-        const int n_act = __popc(amask);
         const int n1 = __popc(amask & __ballot_sync(0xffffffffu, u.kind != 2));
         if ((amask >> lane) & 1u) wq[__popc(amask & lt_mask)] = (uint32_t)lane;
         __syncwarp();
