@@ -268,26 +268,26 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
     auto pivot = [&](int k, const int *rin, int *rout) {      // warp 0 only
         for (int r = lane; r < n; r += 32) rout[r] = rin[r];
         __syncwarp();
-        double best = -1.0;
+        // partial pivoting on |B[r][k]|, compared as the integer bits of |v| plus one (0: NaN or no
+        // row), so the warp reductions run on the integer pipe; ties go to the lowest row
+        unsigned long long best = 0ull;
         int idx = k;
         for (int r = k + lane; r < n; r += 32) {
-            const double v = fabs(B[rout[r] * ld + k]);
-            if (v > best) { best = v; idx = r; }
+            const unsigned long long a =
+                (unsigned long long)__double_as_longlong(B[rout[r] * ld + k]) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long key = a > 0x7FF0000000000000ull ? 0ull : a + 1ull;
+            if (key > best) { best = key; idx = r; }
         }
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, m);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, m);
-            if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
-        }
+        const uint32_t bh = (uint32_t)(best >> 32), bl = (uint32_t)best;
+        const uint32_t mh = __reduce_max_sync(0xffffffffu, bh);
+        const uint32_t ml = __reduce_max_sync(0xffffffffu, bh == mh ? bl : 0u);
+        idx = __reduce_min_sync(0xffffffffu, (bh == mh && bl == ml) ? idx : 0x7FFFFFFF);
         if (lane == 0 && idx != k) { const int t = rout[k]; rout[k] = rout[idx]; rout[idx] = t; }
         __syncwarp();
-        double d = B[rout[k] * ld + k];
-        if (d == 0.0) {
-            if (lane == 0) s_sing = 1;
-            d = 1.0;
-        }
-        const double dinv = 1.0 / d;
+        const double d = B[rout[k] * ld + k];
+        const bool zero = ((unsigned long long)__double_as_longlong(d) << 1) == 0ull;   // +-0
+        if (zero && lane == 0) s_sing = 1;
+        const double dinv = zero ? 1.0 : __drcp_rn(d);
         for (int r = k + 1 + lane; r < n; r += 32) B[rout[r] * ld + k] *= dinv;
     };
     if (n > 0 && warp == 0) pivot(0, perm, perm2);
@@ -324,7 +324,7 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
     if (s_sing && tid == 0) atomicOr(status, VMC_DEV_SINGULAR);
     // reciprocals of U's diagonal (one FP64 division per row, not per element; n <= 128)
     __shared__ double rdiag[VMC_MAX_M / 2];
-    for (int r = tid; r < n; r += nt) rdiag[r] = 1.0 / B[rl[r] * ld + r];
+    for (int r = tid; r < n; r += nt) rdiag[r] = __drcp_rn(B[rl[r] * ld + r]);
     __syncthreads();
     // ---- FP32 copies: unit-lower L, unit-upper U' = D^-1 U, and 1/D; the buffer is reused
     {
@@ -574,6 +574,15 @@ __device__ void refresh_orbitals(int w, int sg, int M, int na, int nb, const uin
     for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
 }
 
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) { return __float_as_uint(v) & 0x7FFFFFFFu; }
+__device__ __forceinline__ unsigned long long abs_inf_bits(double) { return 0x7FF0000000000000ull; }
+__device__ __forceinline__ unsigned long long abs_inf_bits(float) { return 0x7F800000ull; }
+__device__ __forceinline__ double rcp_rn(double d) { return __drcp_rn(d); }
+__device__ __forceinline__ float rcp_rn(float d) { return __frcp_rn(d); }
+
 template <typename real, int R>
 __global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 5 ? 2 : 1))
 k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__restrict__ Cb,
@@ -614,7 +623,9 @@ k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__r
     for (int k = 0; k < n; ++k) {
         const int b = k & 1, kj = k >> 4;
         if (tx == (k & 15)) {                        // pivot search in column k (one half-warp)
-            real best = real(-1), bv = real(0);
+            // candidates: the unused rows; key = |v| bits + 2 (1 for NaN), compared as integers so
+            // the half-warp reductions run on the integer pipe; ties go to the lowest row
+            unsigned long long best = 0ull;
             int bi = kNoRow;
 #pragma unroll
             for (int i = 0; i < R; ++i) {
@@ -624,22 +635,20 @@ k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__r
                     if (j == kj) v = X[i][j];
                 const int r = ty + kGJ * i;
                 if (r < n) pcol[b][r] = v;
-                const real a = v < real(0) ? -v : v;
-                // an unused row always wins over "none" (NaN included), so bi ends as a valid row
-                if (!((used >> i) & 1u) && (bi == kNoRow || a > best)) { best = a; bi = r; bv = v; }
+                const unsigned long long a = abs_bits(v);
+                const unsigned long long key = a > abs_inf_bits(v) ? 1ull : a + 2ull;
+                if (!((used >> i) & 1u) && key > best) { best = key; bi = r; }
             }
-#pragma unroll
-            for (int m = 8; m >= 1; m >>= 1) {
-                const real ob = __shfl_xor_sync(hmask, best, m, 16);
-                const int oi = __shfl_xor_sync(hmask, bi, m, 16);
-                const real ov = __shfl_xor_sync(hmask, bv, m, 16);
-                if (oi != kNoRow && (bi == kNoRow || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; bv = ov; }
-            }
+            const uint32_t bh = (uint32_t)(best >> 32), bl = (uint32_t)best;
+            const uint32_t mh = __reduce_max_sync(hmask, bh);
+            const uint32_t ml = __reduce_max_sync(hmask, bh == mh ? bl : 0u);
+            bi = __reduce_min_sync(hmask, (bh == mh && bl == ml) ? bi : 0x7FFFFFFF);
+            __syncwarp(hmask);
             if (ty == 0) {
-                real d = bv;
+                real d = pcol[b][bi];
                 if (d == real(0) || !isfinite(d)) { s_sing = 1; d = real(1); }
                 s_p[b] = bi;
-                s_d[b] = real(1) / d;
+                s_d[b] = rcp_rn(d);
                 piv[k] = bi;
                 rstep[bi] = k;
             }
