@@ -955,17 +955,16 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
         sp[0] = 0; rk[0] = 1; fr[0][0] = I; to[0][0] = Ao;
         sp[1] = 1; rk[1] = 1; fr[1][0] = Jo - M; to[1][0] = Bo - M;
     }
-    for (int st = 0; st < nsteps; ++st) {
+    // The vectors of step st: ua/ub = R^-1 (G[(a,b),:] - E) with R = G[(a,b), (ci,cj)], the old
+    // columns ci (cj) of G and rows ci (cj) of C_occ^-1.  u2, g2, a2 may be null for a rank-1 step
+    // (then the second term of the update is zero).
+    auto prep = [&](int st, real *u1, real *u2, real *g1, real *g2, real *a1, real *a2) {
         const int s = sp[st], n = geo.n(s), nv = M - n;
-        real *Gs = Gw + geo.g_off(s);
-        real *As = Aw + geo.a_off(s);
-        uint16_t *occs = occ + (s ? geo.na : 0);
-        uint16_t *virts = virt + (s ? geo.nv_a : 0);
+        const real *Gs = Gw + geo.g_off(s);
+        const real *As = Aw + geo.a_off(s);
         const int ci = pos[s * M + fr[st][0]], sa = pos[s * M + to[st][0]] & 0x7FFF;
         int cj = 0, sb = 0;
         if (rk[st] == 2) { cj = pos[s * M + fr[st][1]]; sb = pos[s * M + to[st][1]] & 0x7FFF; }
-        __syncthreads();
-        // R = G[(a,b), (ci,cj)], inverse coefficients; ua/ub = R^-1 (G[(a,b),:] - E)
         real r00 = Gs[(size_t)sa * n + ci], r01 = 0, r10 = 0, r11 = 1;
         if (rk[st] == 2) { r01 = Gs[(size_t)sa * n + cj]; r10 = Gs[(size_t)sb * n + ci]; r11 = Gs[(size_t)sb * n + cj]; }
         const real det = r00 * r11 - r01 * r10;
@@ -973,18 +972,30 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
         for (int c = tid; c < n; c += nt) {
             const real va = Gs[(size_t)sa * n + c] - (c == ci ? (real)1 : (real)0);
             const real vb = rk[st] == 2 ? Gs[(size_t)sb * n + c] - (c == cj ? (real)1 : (real)0) : (real)0;
-            ua[c] = i00 * va + i01 * vb;
-            ub[c] = i10 * va + i11 * vb;
-            ari[c] = As[(size_t)ci * n + c];
-            arj[c] = rk[st] == 2 ? As[(size_t)cj * n + c] : (real)0;
+            u1[c] = i00 * va + i01 * vb;
+            a1[c] = As[(size_t)ci * n + c];
+            if (u2) {
+                u2[c] = i10 * va + i11 * vb;
+                a2[c] = rk[st] == 2 ? As[(size_t)cj * n + c] : (real)0;
+            }
         }
         for (int r = tid; r < nv; r += nt) {
             real x = Gs[(size_t)r * n + ci], y = rk[st] == 2 ? Gs[(size_t)r * n + cj] : (real)0;
             if (r == sa) { x = 1; y = 0; }
             if (rk[st] == 2 && r == sb) { x = 0; y = 1; }
-            gci[r] = x; gcj[r] = y;
+            g1[r] = x;
+            if (g2) g2[r] = y;
         }
-        __syncthreads();
+    };
+    // G <- G - g1 u1^T - g2 u2^T (replaced rows taken as unit vectors), C_occ^-1 likewise
+    auto update = [&](int st, const real *u1, const real *u2, const real *g1, const real *g2, const real *a1,
+                      const real *a2) {
+        const int s = sp[st], n = geo.n(s), nv = M - n;
+        real *Gs = Gw + geo.g_off(s);
+        real *As = Aw + geo.a_off(s);
+        const int ci = pos[s * M + fr[st][0]], sa = pos[s * M + to[st][0]] & 0x7FFF;
+        int cj = 0, sb = 0;
+        if (rk[st] == 2) { cj = pos[s * M + fr[st][1]]; sb = pos[s * M + to[st][1]] & 0x7FFF; }
         typedef typename Vec16<real>::type vec_t;
         constexpr int VE = Vec16<real>::n;
         const bool rk2 = rk[st] == 2;
@@ -992,7 +1003,11 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
             // 16-byte vectors: thread -> fixed column chunk cv, rows r0, r0 + rs, ...
             const int nvc = n / VE, cv = tid % nvc, r0 = tid / nvc, rs = nt / nvc, c0 = cv * VE;
             if (r0 < rs) {
-                const vec_t u = *(const vec_t *)(ua + c0), v = *(const vec_t *)(ub + c0);
+                vec_t zero;
+                real *ze = (real *)&zero;
+#pragma unroll
+                for (int q = 0; q < VE; ++q) ze[q] = real(0);
+                const vec_t u = *(const vec_t *)(u1 + c0), v = u2 ? *(const vec_t *)(u2 + c0) : zero;
                 vec_t *Gv = (vec_t *)Gs;
 #pragma unroll 4
                 for (int r = r0; r < nv; r += rs) {
@@ -1003,13 +1018,13 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
 #pragma unroll
                         for (int q = 0; q < VE; ++q) oe[q] = (c0 + q == cu) ? real(1) : real(0);
                     }
-                    Gv[(size_t)r * nvc + cv] = vfma2(o, gci[r], u, gcj[r], v);
+                    Gv[(size_t)r * nvc + cv] = vfma2(o, g1[r], u, g2 ? g2[r] : real(0), v);
                 }
-                const vec_t a1 = *(const vec_t *)(ari + c0), a2 = *(const vec_t *)(arj + c0);
+                const vec_t b1 = *(const vec_t *)(a1 + c0), b2 = a2 ? *(const vec_t *)(a2 + c0) : zero;
                 vec_t *Av = (vec_t *)As;
 #pragma unroll 4
                 for (int c = r0; c < n; c += rs)
-                    Av[(size_t)c * nvc + cv] = vfma2(Av[(size_t)c * nvc + cv], ua[c], a1, ub[c], a2);
+                    Av[(size_t)c * nvc + cv] = vfma2(Av[(size_t)c * nvc + cv], u1[c], b1, u2 ? u2[c] : real(0), b2);
             }
         } else {
             for (size_t t = tid; t < (size_t)nv * n; t += nt) {
@@ -1017,32 +1032,54 @@ __device__ __forceinline__ void apply_walker(const ListsView &L, const WalkerArg
                 real old = Gs[t];
                 if (r == sa) old = (c == ci) ? (real)1 : (real)0;
                 if (rk2 && r == sb) old = (c == cj) ? (real)1 : (real)0;
-                Gs[t] = old - gci[r] * ua[c] - gcj[r] * ub[c];
+                Gs[t] = old - g1[r] * u1[c] - (g2 ? g2[r] : real(0)) * (u2 ? u2[c] : real(0));
             }
             for (size_t t = tid; t < (size_t)n * n; t += nt) {
                 const int c = (int)(t / n), x = (int)(t % n);
-                As[t] = As[t] - ua[c] * ari[x] - ub[c] * arj[x];
+                As[t] = As[t] - u1[c] * a1[x] - (u2 ? u2[c] : real(0)) * (a2 ? a2[x] : real(0));
             }
         }
+    };
+    // occupation list, virtual list, orbital map and bit string of step st (one thread)
+    auto relist = [&](int st) {
+        const int s = sp[st];
+        uint16_t *occs = occ + (s ? geo.na : 0);
+        uint16_t *virts = virt + (s ? geo.nv_a : 0);
+        const int ci = pos[s * M + fr[st][0]], sa = pos[s * M + to[st][0]] & 0x7FFF;
+        int cj = 0, sb = 0;
+        if (rk[st] == 2) { cj = pos[s * M + fr[st][1]]; sb = pos[s * M + to[st][1]] & 0x7FFF; }
+        occs[ci] = (uint16_t)to[st][0];
+        virts[sa] = (uint16_t)fr[st][0];
+        posw[s * M + to[st][0]] = (uint16_t)ci;
+        posw[s * M + fr[st][0]] = (uint16_t)(0x8000 | sa);
+        if (rk[st] == 2) {
+            occs[cj] = (uint16_t)to[st][1];
+            virts[sb] = (uint16_t)fr[st][1];
+            posw[s * M + to[st][1]] = (uint16_t)cj;
+            posw[s * M + fr[st][1]] = (uint16_t)(0x8000 | sb);
+        }
+        uint32_t *bw = bits + s * geo.nw;
+        for (int k = 0; k < rk[st]; ++k) {
+            const int f = fr[st][k], tt = to[st][k];
+            bw[f >> 5] &= ~(1u << (f & 31));
+            bw[tt >> 5] |= 1u << (tt & 31);
+        }
+    };
+    __syncthreads();
+    if (nsteps == 2) {   // opposite-spin double: the two spins' rank-1 updates share the phases
+        prep(0, ua, nullptr, gci, nullptr, ari, nullptr);
+        prep(1, ub, nullptr, gcj, nullptr, arj, nullptr);
         __syncthreads();
-        if (tid == 0) {
-            occs[ci] = (uint16_t)to[st][0];
-            virts[sa] = (uint16_t)fr[st][0];
-            posw[s * M + to[st][0]] = (uint16_t)ci;
-            posw[s * M + fr[st][0]] = (uint16_t)(0x8000 | sa);
-            if (rk[st] == 2) {
-                occs[cj] = (uint16_t)to[st][1];
-                virts[sb] = (uint16_t)fr[st][1];
-                posw[s * M + to[st][1]] = (uint16_t)cj;
-                posw[s * M + fr[st][1]] = (uint16_t)(0x8000 | sb);
-            }
-            uint32_t *bw = bits + s * geo.nw;
-            for (int k = 0; k < rk[st]; ++k) {
-                const int f = fr[st][k], tt = to[st][k];
-                bw[f >> 5] &= ~(1u << (f & 31));
-                bw[tt >> 5] |= 1u << (tt & 31);
-            }
-        }
+        update(0, ua, nullptr, gci, nullptr, ari, nullptr);
+        update(1, ub, nullptr, gcj, nullptr, arj, nullptr);
+        __syncthreads();
+        if (tid == 0) { relist(0); relist(1); }
+    } else {
+        prep(0, ua, ub, gci, gcj, ari, arj);
+        __syncthreads();
+        update(0, ua, ub, gci, gcj, ari, arj);
+        __syncthreads();
+        if (tid == 0) relist(0);
     }
 }
 
