@@ -136,8 +136,8 @@ class Clocks:
 # warp instructions (smsp__inst_executed.sum), from the capture summarised in
 # profiles/k_local_energy_mixed_h160_w4096.md.  They describe the kernel source with this digest
 # only; any later change of the kernel's file reports traffic as null until it is captured again.
-ELOC_COUNTERS = {"sha256": "2d8a0830937f13d48b3ca53be04a07e7df3a378dbe6842f34cef5e243eaf0d6c",
-                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80506.7, "l2_bytes_per_walker": 875875.4,
+ELOC_COUNTERS = {"sha256": "2ce2119c06f96ce3069d3b8429e711f38fb44c503e99b0be541f82c9f7cb0725",
+                 "system": "H160", "eps": 1e-6, "dram_bytes_per_walker": 80584.9, "l2_bytes_per_walker": 875568.0,
                  "warp_inst_per_walker": 219949.0}
 
 

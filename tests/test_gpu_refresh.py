@@ -82,8 +82,9 @@ def test_register_refresh(vmc, case, precision):
         eng.close()
 
 
-# (system, walkers): virtual orbitals per spin 10, 80 (one full tile), 90/95 (two tiles), 8/16
-G_CASES = [("H20", 64), ("ring160_80_80", 24), ("ring120_30_25", 40), ("ring136_128_120", 16)]
+# (system, walkers): virtual orbitals per spin 10, 80 (one full tile), 90/95 (two tiles), 8/16,
+# 179/181 (three tiles, odd n_sigma)
+G_CASES = [("H20", 64), ("ring160_80_80", 24), ("ring120_30_25", 40), ("ring136_128_120", 16), ("ring200_21_19", 8)]
 
 
 def _g_system(name):
