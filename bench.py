@@ -82,6 +82,21 @@ def load_system(name: str):
     return sys_
 
 
+def l2_note(system: str, walkers: int) -> str:
+    """Whether the walker tables (G and C_occ^-1 per spin, FP32 in the mixed form) exceed the 129 MB
+    L2, so that every sweep streams them from HBM without an L2 flush between steps."""
+    sys_ = S.named_system(system) if system.startswith("hubbard") else None
+    if sys_ is None:
+        M = int(system[1:]) if system.startswith("H") else 0
+        na = nb = M // 2
+    else:
+        M, na, nb = sys_.M, sys_.n_alpha, sys_.n_beta
+    tables = 4 * walkers * ((M - na) * na + (M - nb) * nb + na * na + nb * nb)
+    if tables > 129e6:
+        return f"inputs larger than L2 (walker tables {tables / 1e9:.2f} GB in FP32, no flush needed)"
+    return f"walker tables fit in L2 ({tables / 1e6:.1f} MB in FP32): a small case, not a timing configuration"
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -338,7 +353,7 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False, cps=None)
     for it in range(args.warmup):
         run_step(timed=False, e2e=False, it=it)
     overflow |= sync_counting_overflow(vmc, eng)
-    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     dev_ms, e2e_ms = [], []
     # device-timed and end-to-end loops in the order d e | e d | d e | ...: every step moves the
@@ -395,6 +410,15 @@ def run_form(args, sys_, prm, occ, precision, rank, world, gj32=False, cps=None)
                e_start=e_start, rate_overflow=overflow,
                lists=dict(singles=n_singles, same=n_same, opposite=n_opp), n_params=np_, eloc_threads=eloc_threads,
                h2d=np_ * 8, d2h=(np_ + 2) * 8)
+    if world > 1:
+        # the replicas of the parameters must stay identical on every rank (the same reduced
+        # gradient, the same AMSGrad update): compare each rank's copy with rank 0's
+        import torch.distributed as dist
+        ref = eng.p.clone()
+        dist.broadcast(ref, 0)
+        bad = torch.tensor([0.0 if torch.equal(ref, eng.p) else 1.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(bad, op=dist.ReduceOp.MAX)
+        res["replicas_identical"] = bool(bad.item() == 0.0)
     del graph
     eng.close()
     del eng
@@ -574,8 +598,10 @@ def main():
     if world > 1 and args.impl != "reference":
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        dist.init_process_group("nccl")
+        # one rank per GPU; VMC_DIST_BACKEND=gloo runs the same exchange through host memory, which
+        # also lets several ranks share one GPU (their kernels never wait on one another)
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)) % torch.cuda.device_count())
+        dist.init_process_group(os.environ.get("VMC_DIST_BACKEND", "nccl"))
     if args.eps_sweep:
         if rank == 0:
             eps_study(args)
@@ -583,10 +609,11 @@ def main():
     config = {"workload": f"{args.system} chain STO-3G 1.8 bohr Loewdin, eps={args.eps:g}, "
                           f"{args.walkers} walkers/GPU, {args.sweeps} CTMC sweeps per optimisation step",
               "walkers_per_gpu": args.walkers, "sweeps_per_step": args.sweeps, "eps": args.eps,
-              "l2": "inputs larger than L2 (walker state > 1 GB)",
+              "l2": l2_note(args.system, args.walkers),
               "launch": "eager" if args.no_graph else "one CUDA graph per optimisation step",
               "parallelism": (f"walkers sharded over {world} GPUs, one all-reduce of the walker sums per "
-                              f"optimisation step, parameters replicated") if world > 1 else "1 GPU"}
+                              f"optimisation step ({os.environ.get('VMC_DIST_BACKEND', 'nccl')}), "
+                              f"parameters replicated") if world > 1 else "1 GPU"}
 
     sys_ = load_system(args.system)
     prm = S.make_params(sys_, seed=args.seed)
@@ -667,6 +694,8 @@ def main():
             "rate_overflow": {f: r["rate_overflow"] for f, r in results.items()},
             "energy_per_electron": head["energy"] / sys_.n_elec,
             "lists": head["lists"], "n_params": head["n_params"]}
+    if world > 1:
+        line["replicas_identical"] = all(r["replicas_identical"] for r in results.values())
     for f, r in results.items():
         if f != "mixed" or len(results) == 1:
             line[f"{f}_form"] = {"value": r["value"] * scale, "ms_per_step": r["ms_per_step"],
