@@ -18,6 +18,7 @@ namespace {
 constexpr int kM = 128;          // MMA rows (virtual slots, padded)
 constexpr int kThreads = 256;    // eight warps: warp w reads tensor-memory lanes 32 (w % 4)
 constexpr unsigned kMaxSpin = 1u << 20;
+constexpr int kPreChunks = 8;    // k_g_umma: 16-byte chunks per thread held for the next item
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -95,6 +96,54 @@ __device__ __forceinline__ void stage_tile(const float *__restrict__ src, int ld
     }
 }
 
+// The same work split in two halves, for one pass (chunks <= kPre * blockDim.x): the global loads of
+// a tile into registers, and later the split into hi/lo tiles in shared memory.  Between the two the
+// loads stay in flight, so a persistent kernel can fetch its next item while it works on this one.
+template <int kPre>
+__device__ __forceinline__ void load_tile_regs(const float *__restrict__ src, int ld, int nrows, int ncols, int Kp,
+                                               float4 (&v)[kPre]) {
+    const int kp4 = Kp >> 2, rg_n = (nrows + 7) >> 3;
+    const int chunks = rg_n * kp4 * 8;
+    const bool vec = (ld & 3) == 0 && (((uintptr_t)src) & 15) == 0;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < chunks) {
+            const int r8 = e & 7, cm = e >> 3, kc = cm % kp4, rg = cm / kp4;
+            const int row = rg * 8 + r8, k = kc * 4;
+            if (row < nrows) {
+                if (vec && k + 3 < ncols) {
+                    v[u] = __ldg((const float4 *)(src + (size_t)row * ld + k));
+                } else {
+                    float t[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) t[q] = (k + q < ncols) ? src[(size_t)row * ld + k + q] : 0.f;
+                    v[u] = make_float4(t[0], t[1], t[2], t[3]);
+                }
+            }
+        }
+    }
+}
+
+template <int kPre>
+__device__ __forceinline__ void store_tile_regs(const float4 (&v)[kPre], int nrows, int Kp, unsigned char *hi_t,
+                                                unsigned char *lo_t) {
+    const int chunks = ((nrows + 7) >> 3) * (Kp >> 2) * 8;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        if (e < chunks) {
+            float4 h, l;
+            split_tf32(v[u].x, h.x, l.x); split_tf32(v[u].y, h.y, l.y);
+            split_tf32(v[u].z, h.z, l.z); split_tf32(v[u].w, h.w, l.w);
+            const uint32_t o = (uint32_t)e * 16;
+            *(float4 *)(hi_t + o) = h;
+            *(float4 *)(lo_t + o) = l;
+        }
+    }
+}
+
 // Bounded wait on an mbarrier phase; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     uint32_t done = 0;
@@ -113,6 +162,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
 // A and the tensor-memory accumulator are double buffered: staging item i+1 and draining item i-1
 // overlap the MMAs of item i.  Rows n..127 of the A tile are never written: they read whatever
 // follows in shared memory and only feed output rows that are discarded.
+// kPre > 0 (an item's A tile in at most kPre 16-byte chunks per thread, and M <= kThreads): the
+// global loads of item i+1's A tile and orbital map are issued into registers right after item i
+// is staged, so their latency overlaps item i's MMAs and item i-1's epilogue.
+template <int kPre>
 __global__ void __launch_bounds__(kThreads, 1)
 k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint16_t *__restrict__ pos_all,
          const float *__restrict__ AinvT, float *__restrict__ G, unsigned *status, int lbo_k_major) {
@@ -148,6 +201,15 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
     const uint32_t tmem = tmem_base;
     uint32_t phase[2] = {0u, 0u};
     int cur_spin = -1, prev = -1, prev_buf = 0, it = 0;
+    float4 pre[kPre > 0 ? kPre : 1];   // the next item's A tile chunks (kPre > 0)
+    uint16_t pre_pos = 0;              // and its orbital-map entry tid
+    auto load_item = [&](int t) {
+        const int s = t >= W, w = t - s * W, n = s ? nb : na;
+        if constexpr (kPre > 0)
+            load_tile_regs<kPre>(AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0), n, n, n, Kp, pre);
+        pre_pos = tid < M ? pos_all[(size_t)w * 2 * M + (size_t)s * M + tid] : (uint16_t)0;
+    };
+    if (kPre > 0) load_item(t0);
 
     // epilogue of item q (accumulator buffer bq): G[w][slot(k)][c] = D[c][k] for virtual k
     auto epilogue = [&](int q, int bq) {
@@ -207,10 +269,16 @@ k_g_umma(int W, int M, int na, int nb, const float *__restrict__ Cf, const uint1
         }
         // stage A = AinvT of item t into buffer `buf`, and its orbital map
         unsigned char *Ah = Abuf + (size_t)(2 * buf) * a_bytes, *Al = Ah + a_bytes;
-        const float *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
-        stage_tile<8>(At, n, n, n, Kp, Ah, Al);
-        const uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)s * M;
-        for (int k = tid; k < M; k += kThreads) posb[buf * M + k] = pw[k];
+        if constexpr (kPre > 0) {
+            store_tile_regs<kPre>(pre, n, Kp, Ah, Al);
+            if (tid < M) posb[buf * M + tid] = pre_pos;
+            if (t + 1 < t1) load_item(t + 1);
+        } else {
+            const float *At = AinvT + (size_t)w * astride + (s ? (size_t)na * na : 0);
+            stage_tile<8>(At, n, n, n, Kp, Ah, Al);
+            const uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)s * M;
+            for (int k = tid; k < M; k += kThreads) posb[buf * M + k] = pw[k];
+        }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -838,11 +906,24 @@ vmc_status launch_g_umma(vmc_ctx *ctx, const vmc_walkers *Wk, const float *Cf) {
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_g_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // register prefetch of the next item when an A tile fits in kPreChunks 16-byte chunks per thread
+    const int nmax = na > nb ? na : nb, Kp = (nmax + 7) & ~7;
+    const bool pre = ((nmax + 7) / 8) * (Kp / 4) * 8 <= kPreChunks * kThreads && M <= kThreads;
     const int grid = std::min(nsm, 2 * Wk->W);
-    if (e == cudaSuccess)
-        k_g_umma<<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Cf, Wk->pos, (const float *)Wk->AinvT,
-                                                        (float *)Wk->G, ctx->d_status, 1);
+    if (pre) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_g_umma<kPreChunks>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_g_umma<kPreChunks><<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Cf, Wk->pos,
+                                                                        (const float *)Wk->AinvT, (float *)Wk->G,
+                                                                        ctx->d_status, 1);
+    } else {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_g_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_g_umma<0><<<grid, kThreads, smem, ctx->stream>>>(Wk->W, M, na, nb, Cf, Wk->pos, (const float *)Wk->AinvT,
+                                                               (float *)Wk->G, ctx->d_status, 1);
+    }
     ctx->launches += 1;
     if (e == cudaSuccess) e = cudaGetLastError();
     return cuda_check(ctx, e, "k_g_umma");
