@@ -200,6 +200,10 @@ k_init_tables(int M, int na, int nb, const double *__restrict__ Ca, const double
     }
 }
 
+__device__ void refresh_orbitals(int w, int sg, int M, int na, int nb, const uint16_t *occ_list,
+                                 uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, uint16_t *s_occ,
+                                 uint16_t *s_virt, uint8_t *mark);
+
 // Mixed form: LU of C_occ^T with partial pivoting in FP64 (in shared memory), then the inverse
 // from the factors and G = C C_occ^-1 in FP32, the precision these tables are kept in.
 // Shared memory: one n x (n+1) FP64 buffer; after the factorisation it is reused as two FP32
@@ -223,43 +227,16 @@ k_init_tables_mixed(int M, int na, int nb, const double *__restrict__ Ca, const 
     __shared__ uint8_t mark[VMC_MAX_M];
     __shared__ int perm[VMC_MAX_M];
     __shared__ int s_sing;
-    const uint16_t *occ = occ_list + (size_t)w * ne + (sg ? na : 0);
-    uint16_t *vl = virt_list + (size_t)w * (2 * M - ne) + (sg ? M - na : 0);
-    for (int k = tid; k < M; k += nt) mark[k] = 0;
+    (void)ne; (void)nw; (void)nv;
     if (tid == 0) s_sing = 0;
-    __syncthreads();
-    for (int c = tid; c < n; c += nt) {
-        s_occ[c] = occ[c];
-        mark[occ[c]] = 1;
-        perm[c] = c;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int v = 0;
-        for (int k = 0; k < M; ++k)
-            if (!mark[k]) s_virt[v++] = (uint16_t)k;
-    }
-    for (int q = tid; q < nw; q += nt) {
-        uint32_t word = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int k = q * 32 + b;
-            if (k < M && mark[k]) word |= 1u << b;
-        }
-        occ_bits[((size_t)w * 2 + sg) * nw + q] = word;
-    }
-    for (int t = tid; t < n * n; t += nt) {       // B = C_occ^T: B[x][c] = C[occ[c]][x]
-        const int x = t / n, c = t % n;
+    // occupied/virtual lists, occupation words and the orbital map (ends with a barrier after s_occ)
+    refresh_orbitals(w, sg, M, na, nb, occ_list, virt_list, pos_all, occ_bits, s_occ, s_virt, mark);
+    for (int c = tid; c < n; c += nt) perm[c] = c;
+    for (int t = tid; t < n * n; t += nt) {       // B = C_occ^T: B[x][c] = C[occ[c]][x], read along rows of C
+        const int c = t / n, x = t % n;
         B[x * ld + c] = C[(size_t)s_occ[c] * n + x];
     }
     __syncthreads();
-    {
-        uint16_t *pw = pos_all + (size_t)w * 2 * M + (size_t)sg * M;
-        for (int s = tid; s < nv; s += nt) {
-            vl[s] = s_virt[s];
-            pw[s_virt[s]] = (uint16_t)(0x8000 | s);
-        }
-        for (int c = tid; c < n; c += nt) pw[s_occ[c]] = (uint16_t)c;
-    }
     // ---- LU with partial pivoting, FP64: P B = L U, rows left in place (row list rl: rl[k] = the
     //      row that is pivot k).  Look-ahead: while warps 1.. update columns k+2.. of step k, warp 0
     //      updates column k+1, picks the pivot of step k+1 into the other row list and scales its
@@ -777,8 +754,9 @@ __global__ void k_convert_c(int M, int na, int nb, const double *__restrict__ Ca
 }
 
 // Jastrow sums S_p, and (full init only) Fock sums and the diagonal energy.
-// Jastrow sums S_p = sum_{k occ, k != p} J_kp for a block of kSumWalkers walkers: each row of the
-// symmetric J copy is read once per block and added to every walker that occupies that orbital.
+// Jastrow sums S_p = sum_{k occ, k != p} J_kp for a block of kSumWalkers walkers (thread = p): each
+// walker's occupied rows of the symmetric J copy are added in ascending order, one add per
+// occupied orbital (the rows are L2 resident).
 // (Full init only:) Fock sums F and the diagonal energy, one walker per block.
 constexpr int kSumWalkers = 8;
 
@@ -793,23 +771,35 @@ k_jastrow_sums(int W, int M, const real *__restrict__ Jsym, const uint32_t *__re
     }
     __syncthreads();
     for (int p = threadIdx.x; p < N2; p += blockDim.x) {
-        real acc[kSumWalkers];
-#pragma unroll
-        for (int k = 0; k < kSumWalkers; ++k) acc[k] = 0;
-        for (int r = 0; r < N2; ++r) {
-            const int s = r >= M, kk = r - s * M;
-            const real j = Jsym[(size_t)r * N2 + p];
-#pragma unroll
-            for (int k = 0; k < kSumWalkers; ++k)
-                if ((bits[k][s * nw + (kk >> 5)] >> (kk & 31)) & 1u) acc[k] += j;
-        }
         const real jd = Jsym[(size_t)p * N2 + p];
         const int sp = p >= M, kp = p - sp * M;
-#pragma unroll
         for (int k = 0; k < kSumWalkers; ++k) {
             if (w0 + k >= W) break;
+            // only the walker's occupied spin orbitals r, in ascending order (the set bits of its
+            // alpha words, then of its beta words): one add each, four row loads in flight at a time
+            real acc = 0;
+            for (int q = 0; q < 2 * nw; ++q) {
+                uint32_t word = bits[k][q];
+                const int base = q < nw ? 32 * q : M + 32 * (q - nw);
+                while (word) {
+                    int r[4], m = 0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (word) {
+                            r[u] = base + __ffs(word) - 1;
+                            word &= word - 1u;
+                            m = u + 1;
+                        }
+                    real j[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) j[u] = u < m ? Jsym[(size_t)r[u] * N2 + p] : real(0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u < m) acc += j[u];
+                }
+            }
             const bool occp = (bits[k][sp * nw + (kp >> 5)] >> (kp & 31)) & 1u;
-            S[(size_t)(w0 + k) * N2 + p] = occp ? acc[k] - jd : acc[k];
+            S[(size_t)(w0 + k) * N2 + p] = occp ? acc - jd : acc;
         }
     }
 }
