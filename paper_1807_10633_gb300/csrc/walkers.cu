@@ -561,7 +561,7 @@ __device__ __forceinline__ double rcp_rn(double d) { return __drcp_rn(d); }
 __device__ __forceinline__ float rcp_rn(float d) { return __frcp_rn(d); }
 
 template <typename real, int R>
-__global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 5 ? 2 : 1))
+__global__ void __launch_bounds__(kGJ * kGJ, sizeof(real) == 4 ? (R <= 5 ? 4 : 2) : (R <= 5 ? 3 : 1))
 k_refresh_gj(int M, int na, int nb, const real *__restrict__ Ca, const real *__restrict__ Cb,
              const uint16_t *occ_list, uint16_t *virt_list, uint16_t *pos_all, uint32_t *occ_bits, real *G,
              real *AinvT, unsigned *status, int do_g) {
