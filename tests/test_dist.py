@@ -50,7 +50,7 @@ def _worker(rank, world, port, n_params, out):
 def test_two_rank_gradient_exchange():
     world, n_params = 2, 257
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of a process that may hold a CUDA context
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, n_params, out), nprocs=world, join=True)
         res = dict(out)

@@ -113,7 +113,7 @@ def _oracle_sharded_loop():
 
 def test_two_rank_optimisation_loop_matches_the_sharded_oracle_loop():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of a process that may hold a CUDA context
         out = mgr.dict()
         mp.spawn(_rank, args=(port, out), nprocs=WORLD, join=True)
         res = dict(out)
