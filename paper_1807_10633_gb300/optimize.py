@@ -33,6 +33,20 @@ class Iteration:
 RATE_OVERFLOW = 6      # VMC_ERR_OVERFLOW
 
 
+@dataclass
+class OptState:
+    """The AMSGrad moments m and v (Eqs. m1-m2) and the index of the next iteration: with the
+    parameters and the walkers, what an interrupted optimisation needs to go on (checkpoint.py)."""
+    m: torch.Tensor
+    v: torch.Tensor
+    next_iter: int = 0
+
+    @classmethod
+    def fresh(cls, eng: vmc.Engine) -> "OptState":
+        z = torch.zeros(eng.n_params, dtype=torch.float64, device=eng.p.device)
+        return cls(z, z.clone(), 0)
+
+
 def alpha_schedule(k: int, alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5) -> float:
     """Step size of iteration k: alpha0 for the first `warm` iterations, then alpha1."""
     return alpha0 if k < warm else alpha1
@@ -41,8 +55,12 @@ def alpha_schedule(k: int, alpha0: float = 0.001, alpha1: float = 0.01, warm: in
 def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_in: int = 0,
              alpha0: float = 0.001, alpha1: float = 0.01, warm: int = 5, beta1: float = 0.1,
              beta2: float = 0.01, n_elec: int | None = None, callback=None,
-             train_jastrow: bool = True) -> list[Iteration]:
+             train_jastrow: bool = True, state: OptState | None = None) -> list[Iteration]:
     """Run n_iter AMSGrad iterations on `eng` (its parameters eng.p are updated in place).
+
+    state: the AMSGrad moments and the index of the first iteration (None: zero moments, iteration
+    0); it is updated in place, so a later call with the same state continues the run (the step
+    size schedule and the CTMC seeds follow the global iteration index).
 
     Each iteration: `sweeps` CTMC steps; the first `burn_in` of them move the walkers without
     entering the sums.  Under an initialised process group the walker sums of all ranks are added
@@ -65,8 +83,10 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     np_ = eng.n_params
     red, AO, AEO, sums = D.sums_buffer(np_, dev)
     g = torch.zeros(np_, dtype=torch.float64, device=dev)
-    m = torch.zeros_like(g)
-    v = torch.zeros_like(g)
+    st = state if state is not None else OptState.fresh(eng)
+    if st.m.numel() != np_ or st.v.numel() != np_:
+        raise ValueError("optimiser state does not match the engine's parameters")
+    m, v = st.m, st.v
     AOv, AEOv = eng.split(AO), eng.split(AEO)
     AOc, AEOc = eng.split_cps(AO), eng.split_cps(AEO)   # correlator coefficients (None without them)
     ne = n_elec or (eng.na + eng.nb)
@@ -74,7 +94,7 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     if torch.distributed.is_available() and torch.distributed.is_initialized():
         rank = torch.distributed.get_rank()
     out = []
-    for k in range(n_iter):
+    for k in range(st.next_iter, st.next_iter + n_iter):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -95,11 +115,12 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
         vmc.vmc_amsgrad_update(eng.ctx, eng.p[j0:], g[j0:], m[j0:], v[j0:], alpha, beta1, beta2)
         vmc.vmc_walkers_refresh(eng.ctx, eng.lists, prm, ws)
         b.record(stream)
-        st = vmc.lib().vmc_sync(eng.ctx)             # waits for the stream, returns and clears the flags
-        if st not in (0, RATE_OVERFLOW):
-            vmc._check(eng.ctx, st)
+        rc = vmc.lib().vmc_sync(eng.ctx)             # waits for the stream, returns and clears the flags
+        if rc not in (0, RATE_OVERFLOW):
+            vmc._check(eng.ctx, rc)
         T, TE = (float(x) for x in sums.cpu())
-        it = Iteration(k, alpha, TE / T, TE / T / ne, T, float(g.norm()), a.elapsed_time(b), st == RATE_OVERFLOW)
+        it = Iteration(k, alpha, TE / T, TE / T / ne, T, float(g.norm()), a.elapsed_time(b), rc == RATE_OVERFLOW)
+        st.next_iter = k + 1
         out.append(it)
         if callback is not None:
             callback(it)

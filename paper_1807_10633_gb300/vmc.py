@@ -471,6 +471,8 @@ class Engine:
         self.ctx = vmc_create(device, stream if stream is not None else torch.cuda.current_stream(device))
         self.lists = vmc_build_screened_lists(self.ctx, system.M, system.h1, system.eri, system.e_core, eps)
         self.cps, self.n_corr, self.n_cps = None, 0, 0
+        self.cps_sites = None if cps is None else [[int(x) for x in st] for st in cps.sites]
+        self.system_name = getattr(system, "name", "")
         parts = [np.asarray(params.J, dtype=np.float64).ravel(), np.asarray(params.C_alpha, dtype=np.float64).ravel(),
                  np.asarray(params.C_beta, dtype=np.float64).ravel()]
         if cps is not None:
