@@ -1,6 +1,7 @@
 """Multi-process host logic of walker sharding (world size 2, gloo on the CPU): the shards cover the
 walkers exactly once, rank seeds differ, the single all-reduce adds every rank's walker sums, and
-the AMSGrad update of the reduced gradient leaves identical parameters on every rank."""
+the AMSGrad update of the reduced gradient leaves identical parameters on every rank; a rank that
+leaves or stalls between steps makes the other rank's exchange end with an error, not a hang."""
 import os
 import socket
 
@@ -78,3 +79,41 @@ def test_walker_shard_partition(W, world):
     assert (seen == 1).all()
     with pytest.raises(ValueError):
         D.walker_shard(W, world, world)
+
+
+def _failing_worker(rank, world, port, mode, out):
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=3))
+    try:
+        red, _, _, sums = D.sums_buffer(8, "cpu")
+        sums.fill_(1.0)
+        if rank == 1:
+            if mode == "exits":
+                return                       # leaves between steps, before the exchange
+            import time
+            time.sleep(6)                    # stalls past the process-group timeout
+            return
+        try:
+            D.allreduce_sums(red)
+            out[rank] = "completed"
+        except RuntimeError as e:            # the exchange ends with an error instead of hanging
+            out[rank] = "error: " + str(e)[:80]
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["exits", "stalls"])
+def test_a_rank_that_leaves_ends_the_exchange_with_an_error(mode):
+    """A rank that leaves (or stops answering) between steps: the other rank's all-reduce of the
+    walker sums raises within the process-group timeout instead of waiting for ever."""
+    import time
+    port = _free_port()
+    t0 = time.monotonic()
+    with mp.get_context("spawn").Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_failing_worker, args=(2, port, mode, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[0].startswith("error"), res
+    assert time.monotonic() - t0 < 60
