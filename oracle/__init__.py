@@ -63,6 +63,8 @@ def lib():
         L.orc_psi.restype = D
         L.orc_ctmc_choose.argtypes = [P, L64, U64, U64, U64, P, P]
         L.orc_ctmc_choose.restype = ct.c_int
+        L.orc_ctmc_choose_u.argtypes = [P, L64, U64, P, P]
+        L.orc_ctmc_choose_u.restype = ct.c_int
         L.orc_grad_logpsi.argtypes = [P, P, D, P, P, P]
         L.orc_grad_logpsi.restype = ct.c_int
         L.orc_grad_cps.argtypes = [P, P, D, P]
@@ -197,6 +199,15 @@ def ctmc_choose(moves: np.ndarray, seed: int, walker: int, step: int):
     k = ct.c_long()
     t = ct.c_double()
     rc = lib().orc_ctmc_choose(_p(moves), moves.size, seed, walker, step, ct.byref(k), ct.byref(t))
+    return rc, k.value, t.value
+
+
+def ctmc_choose_u(moves: np.ndarray, U: int):
+    """The choice rule for a given 64-bit uniform draw U (what ctmc_choose draws from Philox)."""
+    moves = np.ascontiguousarray(moves, dtype=MOVE_DTYPE)
+    k = ct.c_long()
+    t = ct.c_double()
+    rc = lib().orc_ctmc_choose_u(_p(moves), moves.size, U, ct.byref(k), ct.byref(t))
     return rc, k.value, t.value
 
 

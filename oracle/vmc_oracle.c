@@ -516,8 +516,17 @@ static u128 rate_fixed(double r) {
  * exact integer sum).  Returns 0, 1 if no move has a non-zero fixed-point rate, 2 if a rate is
  * too large for the fixed-point range.
  */
+int orc_ctmc_choose_u(const orc_move *moves, long nm, uint64_t U, long *chosen, double *t_res);
+
 int orc_ctmc_choose(const orc_move *moves, long nm, uint64_t seed, uint64_t walker, uint64_t step,
                     long *chosen, double *t_res) {
+    uint64_t ctr[4] = {step, 0, 0, 0}, key[2] = {seed, walker}, x[4];
+    orc_philox4x64(ctr, key, x);
+    return orc_ctmc_choose_u(moves, nm, x[0], chosen, t_res);
+}
+
+/* The same choice for a given uniform 64-bit draw U (word 0 of Philox above). */
+int orc_ctmc_choose_u(const orc_move *moves, long nm, uint64_t U, long *chosen, double *t_res) {
     u128 Q = 0;
     for (long k = 0; k < nm; ++k) {
         double r = fabs(moves[k].ratio);
@@ -528,9 +537,6 @@ int orc_ctmc_choose(const orc_move *moves, long nm, uint64_t seed, uint64_t walk
     if (Q == 0) { *t_res = 0.0; return 1; }
     uint64_t qh = (uint64_t)(Q >> 64), ql = (uint64_t)Q;
     *t_res = 1.0 / ((double)qh + (double)ql * 0x1p-64);
-    uint64_t ctr[4] = {step, 0, 0, 0}, key[2] = {seed, walker}, x[4];
-    orc_philox4x64(ctr, key, x);
-    const uint64_t U = x[0];
     /* T = floor(U * Q / 2^64): U*Q = U*qh*2^64 + U*ql */
     u128 T = (u128)U * qh + (u128)(((u128)U * ql) >> 64);
     u128 pre = 0;

@@ -47,6 +47,12 @@ MUTANTS = [
      lambda: P.test_philox_matches_numpy((1807, 123456), (99, 1, 2, 3))),
     ("CTMC choice uniform over moves instead of by rate",
      "pre += rate_fixed(fabs(moves[k].ratio));", "pre += Q / (u128)nm;", P.test_ctmc_choice_distribution),
+    ("choice rule takes the first prefix at or above T instead of above it",
+     "if (pre > T) { *chosen = k; return 0; }", "if (pre >= T) { *chosen = k; return 0; }",
+     P.test_ctmc_choice_rule_at_exact_boundaries),
+    ("integer part of Q dropped from T = floor(U Q / 2^64)",
+     "u128 T = (u128)U * qh + (u128)(((u128)U * ql) >> 64);", "u128 T = (u128)(((u128)U * ql) >> 64);",
+     P.test_ctmc_choice_rule_at_exact_boundaries),
     ("residence time not inverted",
      "*t_res = 1.0 / ((double)qh + (double)ql * 0x1p-64);", "*t_res = (double)qh + (double)ql * 0x1p-64;",
      P.test_ctmc_choice_distribution),

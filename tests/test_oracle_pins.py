@@ -265,6 +265,42 @@ def test_ctmc_choice_distribution():
     assert chi2 < 25.0   # 4 degrees of freedom, p < 1e-4
 
 
+# --- the choice rule at its boundaries, by exact integer arithmetic (reading 6 of Sec. II.B) ---
+def _moves(ratios):
+    mv = np.zeros(len(ratios), dtype=oracle.MOVE_DTYPE)
+    mv["kind"] = 1
+    mv["ratio"] = ratios
+    return mv
+
+
+def test_ctmc_choice_rule_at_exact_boundaries():
+    """q_k = floor(r_k 2^64), Q = sum q_k, T = floor(U Q / 2^64), and the first move whose prefix
+    sum exceeds T (strictly).  Two rates of 1/4 give q = 2^62 each and T = floor(U / 2): U = 2^63
+    puts T exactly on the first prefix (move 1 is chosen), U = 2^63 - 1 just below it (move 0).
+    Rates 1 and 2 give Q = 3 2^64 and T = 3U, so the first prefix 2^64 is crossed between
+    U = floor((2^64 - 1) / 3) and the next U; U = 0 and U = 2^64 - 1 choose the first and the last
+    move with a non-zero rate."""
+    quarter = _moves([0.25, -0.25])
+    assert oracle.ctmc_choose_u(quarter, 2 ** 63)[:2] == (0, 1)
+    assert oracle.ctmc_choose_u(quarter, 2 ** 63 - 1)[:2] == (0, 0)
+    rc, k, t = oracle.ctmc_choose_u(quarter, 0)
+    assert (rc, k) == (0, 0) and t == 2.0
+    big = _moves([1.0, 0.0, -2.0])
+    u = (2 ** 64 - 1) // 3
+    assert oracle.ctmc_choose_u(big, u)[:2] == (0, 0)
+    assert oracle.ctmc_choose_u(big, u + 1)[:2] == (0, 2)
+    assert oracle.ctmc_choose_u(big, 2 ** 64 - 1)[:2] == (0, 2)
+    assert oracle.ctmc_choose_u(big, 0)[2] == 1.0 / 3.0
+    # a rate below 2^-64 has q = 0 and is never chosen; no non-zero rate at all is reported
+    tiny = _moves([0.0, 2.0 ** -70, 0.5])
+    assert oracle.ctmc_choose_u(tiny, 0)[:2] == (0, 2)
+    assert oracle.ctmc_choose_u(_moves([0.0, 2.0 ** -70]), 5)[0] == 1
+    # the Philox form draws U as word 0 of Philox4x64-10(key = (seed, walker), counter = (step, 0, 0, 0))
+    for step in range(5):
+        U = int(oracle.philox4x64([step, 0, 0, 0], [77, 3])[0])
+        assert oracle.ctmc_choose(big, seed=77, walker=3, step=step) == oracle.ctmc_choose_u(big, U)
+
+
 # --- long-run CTMC: the time-weighted histogram converges to rho = psi^2 (Sec. II.B) ----
 def test_ctmc_time_weighted_histogram_converges_to_rho():
     sys = _h4()
