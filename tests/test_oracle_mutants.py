@@ -47,6 +47,9 @@ MUTANTS = [
      lambda: P.test_philox_matches_numpy((1807, 123456), (99, 1, 2, 3))),
     ("CTMC choice uniform over moves instead of by rate",
      "pre += rate_fixed(fabs(moves[k].ratio));", "pre += Q / (u128)nm;", P.test_ctmc_choice_distribution),
+    ("first non-zero pivot instead of the largest in the LU",
+     "if (v > best) { best = v; p = r; }", "if (best == 0.0 && v > best) { best = v; p = r; }",
+     P.test_table_ratios_with_a_tiny_leading_pivot),
     ("choice rule takes the first prefix at or above T instead of above it",
      "if (pre > T) { *chosen = k; return 0; }", "if (pre >= T) { *chosen = k; return 0; }",
      P.test_ctmc_choice_rule_at_exact_boundaries),

@@ -75,6 +75,35 @@ def test_direct_ratios_equal_table_ratios():
         np.testing.assert_allclose(e1, e2, rtol=1e-12)
 
 
+def test_table_ratios_with_a_tiny_leading_pivot():
+    """|psi(m)/psi(n)| from the G table against numpy determinants when C_occ's leading element is
+    1e-17 next to entries of order one: the inverse needs the row exchange of partial pivoting (a
+    first-non-zero pivot keeps the 1e-17 and loses every digit of the inverse's first column)."""
+    sys = _h4()
+    M = sys.M
+    Ca = np.array([[1e-17, 1.0], [1.0, 1.0], [0.3, 0.5], [0.7, -0.2]])
+    Cb = np.array([[0.9, 0.1], [-0.2, 0.8], [0.4, 0.3], [0.1, -0.6]])
+    prm = S.Params(np.zeros((2 * M, 2 * M)), Ca, Cb)
+    orc = Oracle(sys, prm)
+    n = np.zeros(2 * M, dtype=np.uint8)
+    n[[0, 1, M + 0, M + 1]] = 1
+    _, _, mv = orc.local_energy(n, 0.0)
+    assert len(mv) > 0
+
+    def dets(occ):
+        a = sorted(p for p in occ if p < M)
+        b = sorted(p - M for p in occ if p >= M)
+        return np.linalg.det(Ca[a]) * np.linalg.det(Cb[b])
+
+    occ0 = [0, 1, M, M + 1]
+    d0 = dets(occ0)
+    for m in mv:
+        occ = set(occ0) - {int(m["i"])} | {int(m["a"])}
+        if m["kind"] == 2:
+            occ = occ - {int(m["j"])} | {int(m["b"])}
+        assert abs(abs(m["ratio"]) - abs(dets(occ) / d0)) <= 1e-12 * max(1.0, abs(dets(occ) / d0))
+
+
 # --- in-place replacement convention and the a <-> b identity (Sec. III.B, Eq. R) -------
 def test_double_contribution_is_inplace_minor_and_symmetric_in_ab():
     # The oracle's H_nm (explicit canonical phase) times psi(m)/psi(n) equals, for every double,
