@@ -73,3 +73,17 @@ def test_h80_mixed_form_mEh_per_particle(vmc, gj32):
 def test_h80_fp64_form(vmc):
     sys_, prm, occ = make_case("H80", 2048)
     _check(vmc, sys_, prm, occ, 1e-6, 0, idx=np.arange(0, 2048, 131))
+
+
+@pytest.mark.parametrize("precision,gj32", [(0, 0), (1, 0), (1, 1)], ids=["fp64", "mixed_lu64", "mixed_gj32"])
+def test_tiny_leading_pivot_needs_a_row_exchange(vmc, precision, gj32):
+    # C_alpha[0][0] = 1e-17 next to entries of order one: every walker that occupies alpha orbital 0
+    # has C_occ^T[0][0] = 1e-17, which partial pivoting must move away from the diagonal; E_L (from
+    # the G table) against the oracle's, whose LU is pinned against numpy determinants on this case
+    sys_ = S.named_system("H20")
+    prm = S.make_params(sys_, seed=11, j_scale=0.05, c_noise=0.1)
+    occ = S.init_occupations(sys_, prm, 512, seed=12)
+    occ = occ[occ[:, 0] == 0]                # the starts that occupy alpha orbital 0 (about 8 %)
+    assert len(occ) >= 8
+    prm.C_alpha[0, 0] = 1e-17
+    _check(vmc, sys_, prm, occ, 1e-6, precision, gj32=gj32)
