@@ -14,6 +14,10 @@ The mixed-precision form gives `value` (FP32 tables and ratios, C_occ factorised
 refresh, G on the tensor cores); the FP64 form ("fp64_form") and the mixed form with an FP32
 Gauss-Jordan refresh ("mixed_gj32_form") are measured the same way.  `--impl reference` times
 the FP64 CPU oracle instead (a bounded sample).
+
+Under torchrun (N > 1) every rank runs its own walkers and the walker sums are added by one
+all-reduce per step (NCCL; VMC_DIST_BACKEND=gloo uses gloo, which also lets ranks share a GPU);
+the line reports `replicas_identical`, whether every rank's parameters equal rank 0's at the end.
 """
 from __future__ import annotations
 
