@@ -127,9 +127,8 @@ def optimize(eng: vmc.Engine, n_iter: int, sweeps: int, seed: int = 1807, burn_i
     return out
 
 
-def main():
+def parser():
     import argparse
-    import json
 
     from . import systems as S
     ap = argparse.ArgumentParser(description="AMSGrad optimisation of a Jastrow-Slater wavefunction on one GPU")
@@ -144,20 +143,47 @@ def main():
     ap.add_argument("--alpha0", type=float, default=0.001, help="step size of the first --warm iterations")
     ap.add_argument("--alpha1", type=float, default=0.01, help="step size afterwards")
     ap.add_argument("--warm", type=int, default=5)
-    args = ap.parse_args()
+    ap.add_argument("--checkpoint", default="",
+                    help="write a checkpoint to this file at the end (and every --checkpoint-every iterations)")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", default="",
+                    help="continue from this checkpoint (same --system; its form, eps and walkers are kept)")
+    return ap
+
+
+def main(argv=None):
+    import json
+
+    from . import checkpoint as C
+    from . import systems as S
+    args = parser().parse_args(argv)
     sys_ = S.named_system(args.system)
-    prm = S.make_params(sys_, seed=args.seed)
-    occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1)
-    eng = vmc.Engine(sys_, prm, occ, eps=args.eps,
-                     precision=vmc.VMC_MIXED if args.form == "mixed" else vmc.VMC_FP64)
+    if args.resume:
+        eng, st = C.load(args.resume, sys_)
+    else:
+        prm = S.make_params(sys_, seed=args.seed)
+        occ = S.init_occupations(sys_, prm, args.walkers, seed=args.seed + 1)
+        eng = vmc.Engine(sys_, prm, occ, eps=args.eps,
+                         precision=vmc.VMC_MIXED if args.form == "mixed" else vmc.VMC_FP64)
+        st = OptState.fresh(eng)
     vmc.Batch([eng]).autotune()
     t0 = time.perf_counter()
-    its = optimize(eng, args.iters, args.sweeps, seed=args.seed, burn_in=args.burn_in, n_elec=sys_.n_elec,
-                   alpha0=args.alpha0, alpha1=args.alpha1, warm=args.warm,
-                   callback=lambda it: print(json.dumps(it.__dict__), flush=True))
-    print(json.dumps({"system": args.system, "walkers": args.walkers, "sweeps": args.sweeps,
-                      "form": args.form, "eps": args.eps, "wall_s": time.perf_counter() - t0,
-                      "first": its[0].energy_per_electron, "last": its[-1].energy_per_electron}))
+    its = []
+    chunk = args.checkpoint_every if args.checkpoint and args.checkpoint_every > 0 else max(1, args.iters)
+    left = args.iters
+    while left > 0:   # chunks of one run: the state carries the schedule and the seeds across them
+        k = min(chunk, left)
+        its += optimize(eng, k, args.sweeps, seed=args.seed, burn_in=args.burn_in, n_elec=sys_.n_elec,
+                        alpha0=args.alpha0, alpha1=args.alpha1, warm=args.warm, state=st,
+                        callback=lambda it: print(json.dumps(it.__dict__), flush=True))
+        left -= k
+        if args.checkpoint:
+            C.save(args.checkpoint, eng, st, sys_)
+    form = "fp64" if eng.walkers.precision == vmc.VMC_FP64 else "mixed"
+    print(json.dumps({"system": args.system, "walkers": eng.W, "sweeps": args.sweeps, "form": form,
+                      "eps": eng.eps, "wall_s": time.perf_counter() - t0, "next_iter": st.next_iter,
+                      "first": its[0].energy_per_electron if its else None,
+                      "last": its[-1].energy_per_electron if its else None}))
     eng.close()
 
 

@@ -77,3 +77,17 @@ def test_read_refuses_another_system_or_format(tmp_path):
         np.savez(f, **bad)
     with pytest.raises(ValueError, match="format"):
         C.read(tmp_path / "bad.npz", sys_)
+
+
+def test_optimisation_cli_resume_checks_the_system_first(tmp_path):
+    """`python -m paper_1807_10633_gb300.optimize --resume FILE` refuses a checkpoint of another
+    system before any device work; the checkpoint options parse as documented."""
+    from paper_1807_10633_gb300 import optimize as O
+    sys_ = S.named_system("H6")
+    eng, _ = _fake_engine(sys_, 4)
+    st = OptState(torch.zeros(eng.p.numel(), dtype=torch.float64), torch.zeros(eng.p.numel(), dtype=torch.float64))
+    path = C.save(tmp_path / "h6.ckpt", eng, st, sys_)
+    with pytest.raises(ValueError, match="different system"):
+        O.main(["--system", "H4", "--resume", str(path)])
+    a = O.parser().parse_args(["--iters", "7", "--checkpoint", "run.ckpt", "--checkpoint-every", "3"])
+    assert (a.iters, a.checkpoint, a.checkpoint_every, a.resume) == (7, "run.ckpt", 3, "")
