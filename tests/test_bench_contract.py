@@ -61,3 +61,14 @@ def test_ncu_counters_are_reported_only_for_the_captured_kernel_source(monkeypat
     assert bench.counters_apply("H160", 1e-6)
     monkeypatch.setitem(bench.ELOC_COUNTERS, "sha256", "0" * 64)
     assert not bench.counters_apply("H160", 1e-6)
+
+
+def test_l2_note_follows_the_walker_tables():
+    """The config's L2 statement: the H160 benchmark's walker tables (G and C_occ^-1 of both spins,
+    FP32) are 3.36 GB, far above the 129 MB L2, so no flush is needed between timed steps; a small
+    case is labelled as one."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    big = bench.l2_note("H160", 32768)
+    assert big.startswith("inputs larger than L2") and "3.36 GB" in big
+    assert bench.l2_note("H20", 512).startswith("walker tables fit in L2")
